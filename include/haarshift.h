@@ -1,0 +1,200 @@
+/*
+ * haarshift.h - C ABI of the Haar-domain phase-shift and shading library
+ * (sm_103a).
+ *
+ * What it computes (Alnasser & Foroosh, "Non-Linear Phase-Shifting of Haar
+ * Wavelets for Run-Time All-Frequency Lighting"):
+ *
+ *  - haar_shift: the Haar coefficients of a lat-long lighting map after a
+ *    translation (linear phase shift) or a rotation g(theta, phi) =
+ *    f(Theta, Phi) (non-linear phase shift, Sec. "Rotating Haar",
+ *    Eq. tRot/theta/phi/compfunc), computed from the coefficients of the
+ *    original map.
+ *  - shade_vertices: the per-vertex light-transport integral as the double
+ *    product of shifted lighting coefficients and each vertex's Haar
+ *    transport vector (Eq. 1-3 with BRDF x cosine x visibility folded into one
+ *    transfer function; Parseval for orthonormal Haar bases).
+ *
+ * Conventions shared by every entry point
+ *  - Map: H x W lat-long map, H = 2^n (1 <= n <= 12), W = H or 2H; rows are
+ *    elevation theta_i = (i + 1/2) pi / H, columns azimuth
+ *    phi_j = (j + 1/2) 2 pi / W; d = (sin t sin p, cos t, sin t cos p), Y up.
+ *  - Haar: orthonormal non-standard 2-D Haar.  On 2x2 blocks (a b / c d):
+ *    A = (a+b+c+d)/2, H = (b+d-a-c)/2, V = (c+d-a-b)/2, D = (a+d-b-c)/2.
+ *    Canonical order of the N = H W coefficients: A_n (W/H values), then for
+ *    l = n..1 the bands H_l, V_l, D_l, each row-major; band b of level l
+ *    occupies [g (1+b), g (2+b)) with g = (W/H) 4^(n-l).
+ *  - Resampling: bilinear between pixel centres of the map extended across
+ *    its borders: azimuth cyclic; SPHERE: a row beyond a pole is the mirrored
+ *    row half a turn away; TORUS: rows cyclic.
+ *  - Memory: every pointer argument is caller-owned device memory unless a
+ *    comment says otherwise; the library never frees caller memory.  Plans
+ *    own their workspace (allocated in haar_shift_plan, freed in
+ *    haar_shift_plan_destroy).
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Compute entry points are asynchronous, allocate nothing and do not
+ *    synchronise; a plan's workspace is shared by all calls on that plan,
+ *    so calls on one plan must be ordered (same stream, or synchronised).
+ *  - Errors: arguments are validated before any launch; a failing call
+ *    returns a non-zero haar_status_t and haar_last_error() (thread-local)
+ *    describes it.  Setting the environment variable HAAR_FAULT_INJECT to an
+ *    entry point's name makes that entry point return HAAR_ERR_INJECTED
+ *    before launching anything (host-side fault injection for tests).
+ */
+#ifndef HAARSHIFT_H
+#define HAARSHIFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HAAR_API __attribute__((visibility("default")))
+#else
+#define HAAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HAAR_OK = 0,
+  HAAR_ERR_INVALID_ARG = 1, /* bad size, null pointer, misalignment, bad enum */
+  HAAR_ERR_UNSUPPORTED = 2, /* valid but not implemented combination */
+  HAAR_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
+  HAAR_ERR_TIMEOUT = 4,     /* a device-side bounded wait gave up */
+  HAAR_ERR_INJECTED = 5,    /* HAAR_FAULT_INJECT named this entry point */
+  HAAR_ERR_NOMEM = 6        /* workspace allocation failed */
+} haar_status_t;
+
+typedef enum {
+  HAAR_SHIFT_TRANSLATE = 0,   /* params [S][2] float64: (dx, dy) in pixels */
+  HAAR_SHIFT_ROTATE = 1,      /* params [S][9] float64: R row-major, p' = R p */
+  HAAR_SHIFT_ROTATE_EULER = 2 /* params [S][3] float64: (alpha, beta, gamma),
+                                 R = Rz(gamma) Ry(beta) Rx(alpha) (Eq. tRot) */
+} haar_shift_kind_t;
+
+typedef enum { HAAR_BOUNDARY_SPHERE = 0, HAAR_BOUNDARY_TORUS = 1 } haar_boundary_t;
+
+typedef enum {
+  HAAR_OUT_F32 = 0,       /* float32 */
+  HAAR_OUT_BF16_HILO = 1, /* two bfloat16 planes: hi = bf16(x), lo = bf16(x - hi);
+                             the lo plane follows the hi plane (S*C*K elements) */
+  HAAR_OUT_F16 = 2        /* IEEE binary16 */
+} haar_out_t;
+
+typedef enum {
+  HAAR_LAYOUT_SCK = 0, /* out[s][c][k] */
+  HAAR_LAYOUT_SKC = 1, /* out[s][k][c]  (channels interleaved) */
+  HAAR_LAYOUT_KSC = 2  /* out[k][s][c]  (coefficient-major) */
+} haar_layout_t;
+
+typedef struct haar_shift_plan_s* haar_shift_plan_t;
+
+typedef struct {
+  int height;     /* H = 2^n */
+  int width;      /* W in {H, 2H} */
+  int channels;   /* C, 1..64 */
+  int kind;       /* haar_shift_kind_t */
+  int boundary;   /* haar_boundary_t */
+  int max_shifts; /* largest S any call on this plan will pass (workspace size) */
+  int out_coeffs; /* K: the K lowest canonical coefficients are written (0 = all) */
+  int out_type;   /* haar_out_t */
+  int out_layout; /* haar_layout_t */
+} haar_shift_desc_t;
+
+/* Create a plan: validates the descriptor and allocates its device workspace
+ * (pixel map C*H*W floats, per-shift tables and counters, shade_batch's
+ * lighting buffer) on the current device.  *out receives the plan. */
+HAAR_API haar_status_t haar_shift_plan(const haar_shift_desc_t* desc, haar_shift_plan_t* out);
+
+/* Release a plan and its workspace (synchronises the device first). */
+HAAR_API haar_status_t haar_shift_plan_destroy(haar_shift_plan_t plan);
+
+/* The phase shift (Sec. "Rotating Haar" and "Mathematical description";
+ * Sec. "Algorithmic optimization" for the O(N) cost):
+ *   coeffs_out[s] = Haar( resample_s( Haar^-1(coeffs_in) ) ),  s = 0..S-1.
+ * coeffs_in : [C][N] float32, canonical order.
+ * params    : device float64, layout given by the plan's kind (see
+ *             haar_shift_kind_t); translations may be any real numbers.
+ * S         : 1..max_shifts.
+ * coeffs_out: K coefficients per (s, c) in the plan's out_type and layout.
+ * Integer shifts whose components are multiples of a level's block side 2^l
+ * reproduce that level's coefficients as an exact signed permutation of the
+ * input (bit-for-bit).  Uses the plan workspace: calls on one plan must not
+ * overlap on the GPU. */
+HAAR_API haar_status_t haar_shift(haar_shift_plan_t plan, const float* coeffs_in, const double* params,
+                         int S, void* coeffs_out, void* stream);
+
+/* Forward orthonormal Haar transform of `batch` H x W float32 maps
+ * ([batch][H][W] row-major) into [batch][N] canonical coefficients; `scale`
+ * multiplies every output (1.0 for the plain transform). */
+HAAR_API haar_status_t haar_forward(int H, int W, int batch, const float* maps, float* coeffs, float scale,
+                           void* stream);
+
+/* Inverse transform: [batch][N] coefficients -> [batch][H][W] maps. */
+HAAR_API haar_status_t haar_inverse(int H, int W, int batch, const float* coeffs, float* maps,
+                           void* stream);
+
+typedef enum {
+  HAAR_T_DENSE_F32 = 0,     /* vals [V][K] float32, lowest K coefficients */
+  HAAR_T_DENSE_BF16 = 1,    /* vals [V][K] bfloat16, lowest K coefficients */
+  HAAR_T_CSR_F32_U16 = 2,   /* vals float32, idx uint16, rowptr int32 [V+1] */
+  HAAR_T_BINCSR_F16_U32 = 3 /* vals [V][bins][K] binary16, idx [V][bins][K] uint32,
+                               bin_of [S][V] uint8 selects the bin of (s, v) */
+} haar_transport_kind_t;
+
+typedef struct {
+  int kind;                    /* haar_transport_kind_t */
+  int V;                       /* vertices */
+  int K;                       /* dense: coefficients per row; BINCSR: entries per bin */
+  int bins;                    /* BINCSR only */
+  const void* vals;            /* device */
+  const void* idx;             /* device (CSR, BINCSR) */
+  const int32_t* rowptr;       /* device (CSR) */
+  const uint8_t* bin_of;       /* device (BINCSR) */
+} haar_transport_desc_t;
+
+/* The double product (Eq. 2-5 with two factors, Parseval):
+ *   radiance[v][s][c] = sum_k T[v][k] * L'[s][c][k].
+ * lighting: the output of haar_shift on this plan (its out_type/layout).
+ * Supported pairings (others return HAAR_ERR_UNSUPPORTED):
+ *   DENSE_F32        with F32  lighting, layout SCK, K <= plan K;
+ *   DENSE_BF16       with BF16_HILO lighting, layout SCK, K == plan K,
+ *                    K % 64 == 0 (tcgen05 tensor-core GEMM, FP32 accumulate,
+ *                    T x L_hi + T x L_lo);
+ *   CSR_F32_U16      with F32  lighting, layout KSC (S*C % 4 == 0);
+ *   BINCSR_F16_U32   with F32  lighting, layout SKC.
+ * radiance: [V][S][C] float32, overwritten. */
+HAAR_API haar_status_t shade_vertices(haar_shift_plan_t plan, const haar_transport_desc_t* transport,
+                             const void* lighting, int S, float* radiance, void* stream);
+
+/* haar_shift followed by shade_vertices, with the shifted lighting kept in
+ * the plan's workspace (stream-ordered, no host synchronisation). */
+HAAR_API haar_status_t shade_batch(haar_shift_plan_t plan, const float* coeffs_in, const double* params,
+                          int S, const haar_transport_desc_t* transport, float* radiance,
+                          void* stream);
+
+/* View-bin selection for view-dependent transport (the paper's per-pixel
+ * "BRDF tile id" of the rotation input pass, Sec. "Experimental results"):
+ * for every (s, v) the bin whose local direction has the largest dot product
+ * with the vertex's local view direction normalize(cam[s] - pos[v]),
+ * expressed in the frame (b1, b2, n) of the branchless orthonormal basis of
+ * Duff et al. 2017; ties keep the lower bin.  pos, nrm: [V][3] float32;
+ * cams: [S][3] float32; bin_dirs: [bins][3] float32 (local, z = normal);
+ * bin_of: [S][V] uint8 (bins <= 255). */
+HAAR_API haar_status_t haar_view_bins(int V, int S, int bins, const float* pos, const float* nrm,
+                             const float* cams, const float* bin_dirs, uint8_t* bin_of,
+                             void* stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+HAAR_API const char* haar_last_error(void);
+
+/* Library version string. */
+HAAR_API const char* haar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAARSHIFT_H */

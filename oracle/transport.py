@@ -39,15 +39,19 @@ def lowest(T: np.ndarray, K: int) -> np.ndarray:
 
 def topk_csr(T: np.ndarray, K: int):
     """CSR (vals [V*K], idx [V*K], rowptr [V+1]) of the K largest |T| per row;
-    equal magnitudes keep the lower index; every row sorted by index."""
+    among equal magnitudes the lower index is kept; every row sorted by index."""
     T = np.asarray(T)
     V, N = T.shape
-    # stable sort on -|T| keeps the lower index first among equal magnitudes
-    order = np.argsort(-np.abs(T), axis=1, kind="stable")[:, :K]
-    idx = np.sort(order, axis=1)
-    vals = np.take_along_axis(T, idx, axis=1)
+    a = np.abs(T)
+    kth = np.partition(a, N - K, axis=1)[:, N - K]          # K-th largest magnitude
+    gt = a > kth[:, None]
+    eq = a == kth[:, None]
+    need = K - gt.sum(axis=1)
+    sel = gt | (eq & (np.cumsum(eq, axis=1) <= need[:, None]))
+    rows, cols = np.nonzero(sel)                              # row-major: indices ascend
+    vals = T[rows, cols]
     rowptr = np.arange(V + 1, dtype=np.int64) * K
-    return vals.reshape(-1), idx.reshape(-1), rowptr
+    return vals, cols.astype(np.int64), rowptr
 
 
 def csr_dense(vals, idx, rowptr, N: int) -> np.ndarray:
@@ -93,3 +97,37 @@ def split_hilo(x):
 def to_f16(x) -> np.ndarray:
     """IEEE binary16, nearest-even (numpy's conversion), as float64."""
     return np.asarray(np.asarray(x, dtype=np.float64).astype(np.float16), dtype=np.float64)
+
+
+def frame(n: np.ndarray):
+    """Orthonormal tangent frame (b1, b2) around unit normals n [V, 3]: the
+    branchless construction of Duff et al., 'Building an Orthonormal Basis,
+    Revisited' (2017)."""
+    n = np.asarray(n, dtype=np.float64)
+    sign = np.where(n[:, 2] >= 0.0, 1.0, -1.0)
+    a = -1.0 / (sign + n[:, 2])
+    b = n[:, 0] * n[:, 1] * a
+    b1 = np.stack([1.0 + sign * n[:, 0] * n[:, 0] * a, sign * b, -sign * n[:, 0]], axis=1)
+    b2 = np.stack([b, sign + n[:, 1] * n[:, 1] * a, -n[:, 1]], axis=1)
+    return b1, b2
+
+
+def view_bins(pos, nrm, cams, bin_dirs):
+    """(bin_of [S, V], margin [S, V]): for every camera s and vertex v the bin
+    whose local direction has the largest dot product with the local view
+    direction normalize(cam - pos) (lower bin on ties), and the gap between
+    the best and the second-best dot product."""
+    pos = np.asarray(pos, dtype=np.float64)
+    b1, b2 = frame(nrm)
+    n = np.asarray(nrm, dtype=np.float64)
+    out = np.zeros((len(cams), len(pos)), dtype=np.int64)
+    margin = np.zeros((len(cams), len(pos)))
+    for s, cam in enumerate(np.asarray(cams, dtype=np.float64)):
+        w = cam[None, :] - pos
+        w /= np.linalg.norm(w, axis=1, keepdims=True)
+        loc = np.stack([(w * b1).sum(1), (w * b2).sum(1), (w * n).sum(1)], axis=1)
+        d = loc @ np.asarray(bin_dirs, dtype=np.float64).T
+        out[s] = np.argmax(d, axis=1)
+        srt = np.sort(d, axis=1)
+        margin[s] = srt[:, -1] - srt[:, -2] if d.shape[1] > 1 else np.inf
+    return out, margin

@@ -1,0 +1,273 @@
+"""Python binding of libhaarshift.so: the Haar-domain phase shift of a
+lat-long lighting map and the per-vertex double product on sm_103a.
+
+The functions here only marshal arguments (torch tensors -> device pointers,
+the current CUDA stream) into the C ABI declared in include/haarshift.h;
+every step of the computation runs in the library's CUDA kernels.  The
+library must have been built (``paper_1705_07272_gb300.build.build()``);
+importing the binding does not build it and there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libhaarshift.so")
+
+# haar_status_t
+HAAR_OK = 0
+HAAR_ERR_INVALID_ARG = 1
+HAAR_ERR_UNSUPPORTED = 2
+HAAR_ERR_CUDA = 3
+HAAR_ERR_TIMEOUT = 4
+HAAR_ERR_INJECTED = 5
+HAAR_ERR_NOMEM = 6
+# haar_shift_kind_t
+HAAR_SHIFT_TRANSLATE = 0
+HAAR_SHIFT_ROTATE = 1
+HAAR_SHIFT_ROTATE_EULER = 2
+# haar_boundary_t
+HAAR_BOUNDARY_SPHERE = 0
+HAAR_BOUNDARY_TORUS = 1
+# haar_out_t
+HAAR_OUT_F32 = 0
+HAAR_OUT_BF16_HILO = 1
+HAAR_OUT_F16 = 2
+# haar_layout_t
+HAAR_LAYOUT_SCK = 0
+HAAR_LAYOUT_SKC = 1
+HAAR_LAYOUT_KSC = 2
+# haar_transport_kind_t
+HAAR_T_DENSE_F32 = 0
+HAAR_T_DENSE_BF16 = 1
+HAAR_T_CSR_F32_U16 = 2
+HAAR_T_BINCSR_F16_U32 = 3
+
+EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward",
+           "haar_inverse", "shade_vertices", "shade_batch", "haar_view_bins",
+           "haar_last_error", "haar_version")
+
+
+class HaarShiftDesc(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_int), ("width", ctypes.c_int), ("channels", ctypes.c_int),
+                ("kind", ctypes.c_int), ("boundary", ctypes.c_int), ("max_shifts", ctypes.c_int),
+                ("out_coeffs", ctypes.c_int), ("out_type", ctypes.c_int), ("out_layout", ctypes.c_int)]
+
+
+class HaarTransportDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("V", ctypes.c_int), ("K", ctypes.c_int), ("bins", ctypes.c_int),
+                ("vals", ctypes.c_void_p), ("idx", ctypes.c_void_p), ("rowptr", ctypes.c_void_p),
+                ("bin_of", ctypes.c_void_p)]
+
+
+class HaarError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"haarshift status {status}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1705_07272_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    L.haar_shift_plan.argtypes = [ctypes.POINTER(HaarShiftDesc), ctypes.POINTER(vp)]
+    L.haar_shift_plan_destroy.argtypes = [vp]
+    L.haar_shift.argtypes = [vp, vp, vp, i, vp, vp]
+    L.haar_forward.argtypes = [i, i, i, vp, vp, ctypes.c_float, vp]
+    L.haar_inverse.argtypes = [i, i, i, vp, vp, vp]
+    L.shade_vertices.argtypes = [vp, ctypes.POINTER(HaarTransportDesc), vp, i, vp, vp]
+    L.shade_batch.argtypes = [vp, vp, vp, i, ctypes.POINTER(HaarTransportDesc), vp, vp]
+    L.haar_view_bins.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp]
+    for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward", "haar_inverse",
+                 "shade_vertices", "shade_batch", "haar_view_bins"):
+        getattr(L, name).restype = st
+    L.haar_last_error.restype = ctypes.c_char_p
+    L.haar_last_error.argtypes = []
+    L.haar_version.restype = ctypes.c_char_p
+    L.haar_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != HAAR_OK:
+        raise HaarError(status, lib().haar_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _dev(t, dtype=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A haar_shift_plan_t and its descriptor."""
+
+    def __init__(self, height, width, channels, kind=HAAR_SHIFT_TRANSLATE, boundary=HAAR_BOUNDARY_SPHERE,
+                 max_shifts=1, out_coeffs=0, out_type=HAAR_OUT_F32, out_layout=HAAR_LAYOUT_SCK):
+        self.desc = HaarShiftDesc(height, width, channels, kind, boundary, max_shifts, out_coeffs,
+                                  out_type, out_layout)
+        h = ctypes.c_void_p()
+        _check(lib().haar_shift_plan(ctypes.byref(self.desc), ctypes.byref(h)))
+        self.handle = h.value
+        self.H, self.W, self.C = height, width, channels
+        self.N = height * width
+        self.K = out_coeffs or self.N
+        self.kind, self.out_type, self.out_layout = kind, out_type, out_layout
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().haar_shift_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def out_shape(self, S):
+        """Shape of haar_shift's output tensor for S shifts."""
+        planes = 2 if self.out_type == HAAR_OUT_BF16_HILO else 1
+        if self.out_layout == HAAR_LAYOUT_SCK:
+            shp = (S, self.C, self.K)
+        elif self.out_layout == HAAR_LAYOUT_SKC:
+            shp = (S, self.K, self.C)
+        else:
+            shp = (self.K, S, self.C)
+        return ((planes,) + shp) if planes == 2 else shp
+
+    def out_dtype(self):
+        import torch
+        return {HAAR_OUT_F32: torch.float32, HAAR_OUT_BF16_HILO: torch.bfloat16,
+                HAAR_OUT_F16: torch.float16}[self.out_type]
+
+
+def haar_shift_plan(height, width, channels, **kw) -> Plan:
+    return Plan(height, width, channels, **kw)
+
+
+def haar_shift_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def haar_shift(plan: Plan, coeffs_in, params, coeffs_out=None, stream=None):
+    """Shifted coefficients of coeffs_in [C][N] for params [S][2|9|3] (float64)."""
+    import torch
+    S = params.shape[0]
+    if coeffs_out is None:
+        coeffs_out = torch.empty(plan.out_shape(S), dtype=plan.out_dtype(), device=coeffs_in.device)
+    _check(lib().haar_shift(plan.handle, _dev(coeffs_in, torch.float32, "coeffs_in"),
+                            _dev(params, torch.float64, "params"), S, _dev(coeffs_out, None, "coeffs_out"),
+                            _stream(stream)))
+    return coeffs_out
+
+
+def haar_forward(maps, out=None, scale=1.0, stream=None):
+    """Haar coefficients [B][N] of maps [B][H][W] (float32)."""
+    import torch
+    B, H, W = maps.shape
+    if out is None:
+        out = torch.empty((B, H * W), dtype=torch.float32, device=maps.device)
+    _check(lib().haar_forward(H, W, B, _dev(maps, torch.float32, "maps"), _dev(out, torch.float32, "out"),
+                              float(scale), _stream(stream)))
+    return out
+
+
+def haar_inverse(coeffs, H, W, out=None, stream=None):
+    import torch
+    B = coeffs.shape[0]
+    if out is None:
+        out = torch.empty((B, H, W), dtype=torch.float32, device=coeffs.device)
+    _check(lib().haar_inverse(H, W, B, _dev(coeffs, torch.float32, "coeffs"), _dev(out, torch.float32, "out"),
+                              _stream(stream)))
+    return out
+
+
+class Transport:
+    """Device transport storage and its haar_transport_desc_t."""
+
+    def __init__(self, kind, V, K, vals, idx=None, rowptr=None, bins=0, bin_of=None):
+        self.kind, self.V, self.K, self.bins = kind, V, K, bins
+        self.vals, self.idx, self.rowptr, self.bin_of = vals, idx, rowptr, bin_of
+        for name in ("vals", "idx", "rowptr", "bin_of"):
+            t = getattr(self, name)
+            if t is not None:
+                _dev(t, None, name)
+
+    def desc(self) -> HaarTransportDesc:
+        return HaarTransportDesc(self.kind, self.V, self.K, self.bins, _ptr(self.vals), _ptr(self.idx),
+                                 _ptr(self.rowptr), _ptr(self.bin_of))
+
+
+def shade_vertices(plan: Plan, transport: Transport, lighting, S, radiance=None, stream=None):
+    """radiance [V][S][C] = sum_k T[v][k] L'[s][c][k]."""
+    import torch
+    if radiance is None:
+        radiance = torch.empty((transport.V, S, plan.C), dtype=torch.float32, device=lighting.device)
+    d = transport.desc()
+    _check(lib().shade_vertices(plan.handle, ctypes.byref(d), _dev(lighting, None, "lighting"), S,
+                                _dev(radiance, torch.float32, "radiance"), _stream(stream)))
+    return radiance
+
+
+def shade_batch(plan: Plan, coeffs_in, params, transport: Transport, radiance=None, stream=None):
+    """haar_shift then shade_vertices, the shifted lighting kept in the plan."""
+    import torch
+    S = params.shape[0]
+    if radiance is None:
+        radiance = torch.empty((transport.V, S, plan.C), dtype=torch.float32, device=coeffs_in.device)
+    d = transport.desc()
+    _check(lib().shade_batch(plan.handle, _dev(coeffs_in, torch.float32, "coeffs_in"),
+                             _dev(params, torch.float64, "params"), S, ctypes.byref(d),
+                             _dev(radiance, torch.float32, "radiance"), _stream(stream)))
+    return radiance
+
+
+def haar_view_bins(pos, nrm, cams, bin_dirs, out=None, stream=None):
+    """bin_of [S][V] uint8: the view bin of every (s, v)."""
+    import torch
+    V, S, bins = pos.shape[0], cams.shape[0], bin_dirs.shape[0]
+    if out is None:
+        out = torch.empty((S, V), dtype=torch.uint8, device=pos.device)
+    _check(lib().haar_view_bins(V, S, bins, _dev(pos, torch.float32, "pos"), _dev(nrm, torch.float32, "nrm"),
+                                _dev(cams, torch.float32, "cams"), _dev(bin_dirs, torch.float32, "bin_dirs"),
+                                _dev(out, torch.uint8, "bin_of"), _stream(stream)))
+    return out
+
+
+def version() -> str:
+    return lib().haar_version().decode()

@@ -1,0 +1,107 @@
+// Shared declarations of the sm_103a Haar phase-shift library: the plan,
+// per-shift parameter records and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/haarshift.h"
+
+namespace hs {
+
+// Per-shift record built in FP64 by the set-up kernel (the per-launch
+// construction of the shift's mixing weights; the "rotation input pass" of
+// Sec. "Experimental results").
+struct ShiftParam {
+  int kx, ky;                // integer part of the translation (kx in [0,W), ky in [0,period))
+  float wx0, wx1, wy0, wy1;  // bilinear weights: g = wy0 (wx0 F[i-ky][j-kx] + wx1 F[i-ky][j-kx-1])
+                             //                    + wy1 (wx0 F[i-ky-1][j-kx] + wx1 F[i-ky-1][j-kx-1])
+  uint32_t perm_mask;        // bit l (1..n): level l is a signed permutation; bit n+1: scaling
+  int pad;
+  float R[9];                // rotation p' = R p (row-major), float32
+  float pad2[3];
+};
+static_assert(sizeof(ShiftParam) == 80, "ShiftParam layout");
+
+struct Geometry {
+  int H, W, C, n, q;
+  int T, Lt;                 // tile side and the number of levels done inside a tile
+  int tiles_r, tiles_c, n_tiles;
+  int boundary;
+  long long N;               // H * W
+};
+
+static inline Geometry make_geometry(int H, int W, int C, int boundary) {
+  Geometry g;
+  g.H = H; g.W = W; g.C = C; g.boundary = boundary;
+  int n = 0;
+  while ((1 << n) < H) ++n;
+  g.n = n;
+  g.q = W / H;
+  g.T = H < 64 ? H : 64;
+  int lt = 0;
+  while ((1 << lt) < g.T) ++lt;
+  g.Lt = lt;
+  g.tiles_r = H / g.T;
+  g.tiles_c = W / g.T;
+  g.n_tiles = g.tiles_r * g.tiles_c;
+  g.N = (long long)H * W;
+  return g;
+}
+
+}  // namespace hs
+
+struct haar_shift_plan_s {
+  haar_shift_desc_t desc;
+  hs::Geometry geo;
+  int K;                     // coefficients written per (s, c)
+  int device;
+  // workspace (device)
+  float* pix;                // [C][H][W] pixel map synthesised per launch
+  float* trig;               // sin_t[H] cos_t[H] sin_p[W] cos_p[W]
+  hs::ShiftParam* prm;       // [max_shifts]
+  float* means;              // [max_shifts][C][n_tiles]
+  unsigned* counters;        // [max_shifts]
+  void* light;               // shade_batch lighting [max_shifts * C * K] (x2 planes for BF16_HILO)
+  size_t light_elems;        // elements per plane
+  int* status;               // device status word (0 = fine)
+};
+
+namespace hs {
+
+// status helpers (abi.cu)
+haar_status_t set_error(haar_status_t st, const char* fmt, ...);
+haar_status_t cuda_check(cudaError_t e, const char* what);
+bool injected(const char* entry);
+
+// launchers (shift.cu)
+haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const double* params,
+                           int S, cudaStream_t st);
+haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
+                           cudaStream_t st);
+haar_status_t launch_trig(haar_shift_plan_s* p, cudaStream_t st);
+haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* coeffs,
+                             float scale, cudaStream_t st);
+haar_status_t launch_inverse(int H, int W, int batch, const float* coeffs, float* maps,
+                             cudaStream_t st);
+
+// launchers (shade.cu)
+haar_status_t launch_shade_dense_f32(const float* T, int V, int K, const float* L, int ldl,
+                                     int ncols, float* R, cudaStream_t st);
+haar_status_t launch_shade_csr_f32(const float* vals, const uint16_t* idx, const int32_t* rowptr,
+                                   int V, const float* L, int NL, int ncols, float* R, cudaStream_t st);
+haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,
+                                      int V, int bins, int K, int S, int C, const float* L,
+                                      long long NL, float* R, cudaStream_t st);
+haar_status_t launch_view_bins(int V, int S, int bins, const float* pos, const float* nrm,
+                               const float* cams, const float* bin_dirs, uint8_t* bin_of,
+                               cudaStream_t st);
+
+// tensor-core contraction (gemm_tc.cu)
+haar_status_t launch_shade_dense_bf16_tc(const __nv_bfloat16* T, int V, int K,
+                                         const __nv_bfloat16* Lhi, const __nv_bfloat16* Llo,
+                                         int ncols, float* R, int* status, cudaStream_t st);
+
+}  // namespace hs

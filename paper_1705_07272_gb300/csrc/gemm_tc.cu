@@ -1,0 +1,348 @@
+// Dense double product on the 5th-generation tensor cores (tcgen05, sm_103a):
+//   R[v][j] = sum_k T[v][k] * (Lhi[j][k] + Llo[j][k]),   j = s*C + c,
+// with T the per-vertex transport (the lowest K canonical Haar coefficients,
+// bfloat16) and L the shifted lighting split into bfloat16 hi + lo parts, so
+// the product keeps ~16 mantissa bits of the lighting while the transport
+// streams from HBM as bfloat16 (Eq. 2-5 with two factors, Parseval).
+//
+// Persistent, warp-specialised kernel, one CTA per SM:
+//   warp 0     TMA producer: A tile [128 x 64] of T and the B tiles [N x 64]
+//              of Lhi and Llo per k-block into a 3-stage ring (128-byte swizzle);
+//   warp 1     TMEM allocator and MMA issuer: for every k-block 4 x 2
+//              tcgen05.mma (M=128, N, K=16) accumulate T*Lhi + T*Llo into an
+//              FP32 accumulator in tensor memory (two accumulators, so the
+//              epilogue of one vertex tile overlaps the next tile's MMAs);
+//   warps 2-5  epilogue: tcgen05.ld the accumulator rows and store them.
+// Every mbarrier wait is bounded (by %globaltimer); on expiry the kernel
+// records HAAR_ERR_TIMEOUT in the status word, drains what it issued, frees
+// its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace hs {
+namespace tc {
+
+constexpr int BM = 128;            // vertices per tile (MMA M)
+constexpr int BK = 64;             // k per stage: 64 bf16 = one 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int UMMA_K = 16;
+constexpr int THREADS = 192;       // 6 warps
+constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and the status word / abort flag set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status,
+                                          volatile int* abort_flag) {
+  for (int i = 0; i < 256; ++i)
+    if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > TIMEOUT_NS) {
+      atomicOr(status, 1 << HAAR_ERR_TIMEOUT);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);            // start address
+  d |= (uint64_t)1 << 16;                              // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                    // stride byte offset
+  d |= (uint64_t)1 << 46;                              // descriptor version
+  d |= (uint64_t)2 << 61;                              // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: bf16 x bf16 -> f32, K-major A and B.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4)                       // D format f32
+         | (1u << 7)                     // A format bf16
+         | (1u << 10)                    // B format bf16
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct __align__(8) Bars {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
+             const __grid_constant__ CUtensorMap mapBl, int V, int K, int N, float* __restrict__ R,
+             int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ Bars bars;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // 1024-byte aligned ring: per stage A (16 KB) | Bhi (N*128 B) | Blo (N*128 B)
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)N * BK * 2;
+  const uint32_t stage_bytes = a_bytes + 2 * b_bytes;
+  const int n_tiles = (V + BM - 1) / BM;
+  const int kblocks = K / BK;
+  volatile int* abort_flag = &bars.abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars.full[s]), 1);
+      mbar_init(smem_u32(&bars.empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars.tfull[a]), 1);
+      mbar_init(smem_u32(&bars.tempty[a]), 4);
+    }
+    mbar_init(smem_u32(&bars.drain), 1);
+    bars.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {  // whole warp allocates 512 TMEM columns (two N <= 256 accumulators)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&bars.tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = bars.tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapBh)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapBl)) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued[STAGES];
+      uint32_t issued_phase[STAGES];
+      for (int i = 0; i < STAGES; ++i) { issued[i] = 0; issued_phase[i] = 0; }
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(smem_u32(&bars.empty[stage]), phase ^ 1u, status, abort_flag)) { ok = false; break; }
+          const uint32_t sa = base + stage * stage_bytes;
+          const uint32_t fb = smem_u32(&bars.full[stage]);
+          mbar_arrive_tx(fb, stage_bytes);
+          tma_load_2d(sa, &mapA, kb * BK, tile * BM, fb);
+          tma_load_2d(sa + a_bytes, &mapBh, kb * BK, 0, fb);
+          tma_load_2d(sa + a_bytes + b_bytes, &mapBl, kb * BK, 0, fb);
+          issued[stage] = 1;
+          issued_phase[stage] = phase;
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      // every load issued lands before the CTA exits (on the normal path the
+      // MMA thread has already consumed them all and these waits pass at once)
+      for (int i = 0; i < STAGES; ++i) {
+        if (!issued[i]) continue;
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try(smem_u32(&bars.full[i]), issued_phase[i]) && gtimer() - t0 < TIMEOUT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, N);
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+        const int acc = it & 1;
+        const uint32_t accp = (uint32_t)((it >> 1) & 1);
+        if (!mbar_wait(smem_u32(&bars.tempty[acc]), accp ^ 1u, status, abort_flag)) { ok = false; break; }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * 256);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(smem_u32(&bars.full[stage]), phase, status, abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t sa = base + stage * stage_bytes;
+#pragma unroll
+          for (int k = 0; k < BK / UMMA_K; ++k) {
+            const uint64_t da = make_desc(sa + k * UMMA_K * 2);
+            const uint64_t dh = make_desc(sa + a_bytes + k * UMMA_K * 2);
+            const uint64_t dl = make_desc(sa + a_bytes + b_bytes + k * UMMA_K * 2);
+            mma_bf16(d, da, dh, idesc, (kb | k) != 0 ? 1u : 0u);
+            mma_bf16(d, da, dl, idesc, 1u);
+          }
+          mma_commit(smem_u32(&bars.empty[stage]));     // frees the stage when these MMAs finish
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars.tfull[acc]));         // accumulator ready for the epilogue
+      }
+      // all MMAs issued by this thread complete before tensor memory is freed
+      mma_commit(smem_u32(&bars.drain));
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try(smem_u32(&bars.drain), 0) && gtimer() - t0 < TIMEOUT_NS) {
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    const int row_in_tile = quarter * 32 + lane;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+      const int acc = it & 1;
+      const uint32_t accp = (uint32_t)((it >> 1) & 1);
+      if (!mbar_wait(smem_u32(&bars.tfull[acc]), accp, status, abort_flag)) break;
+      fence_after();
+      const long long row = (long long)tile * BM + row_in_tile;
+      const uint32_t t_row = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256);
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(t_row + (uint32_t)c0, v);
+        if (row < V) {
+          float4* dst = reinterpret_cast<float4*>(R + row * N + c0);
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+          dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+          dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars.tempty[acc]));
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+}  // namespace tc
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                      uint32_t box_outer) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+haar_status_t launch_shade_dense_bf16_tc(const __nv_bfloat16* T, int V, int K, const __nv_bfloat16* Lhi,
+                                         const __nv_bfloat16* Llo, int ncols, float* R, int* status,
+                                         cudaStream_t st) {
+  using namespace tc;
+  if (K % BK != 0 || ncols % 16 != 0 || ncols < 16 || ncols > 256)
+    return set_error(HAAR_ERR_UNSUPPORTED, "dense bf16 contraction: K %% 64 == 0 and 16 <= S*C <= 256, S*C %% 16 == 0");
+  CUtensorMap mA, mBh, mBl;
+  if (!encode_2d(&mA, T, (uint64_t)K, (uint64_t)V, BK, BM) ||
+      !encode_2d(&mBh, Lhi, (uint64_t)K, (uint64_t)ncols, BK, (uint32_t)ncols) ||
+      !encode_2d(&mBl, Llo, (uint64_t)K, (uint64_t)ncols, BK, (uint32_t)ncols))
+    return set_error(HAAR_ERR_CUDA, "dense bf16 contraction: cuTensorMapEncodeTiled failed");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = (V + BM - 1) / BM;
+  const int grid = n_tiles < sms ? n_tiles : sms;
+  const size_t smem = (size_t)STAGES * (BM * BK * 2 + 2 * (size_t)ncols * BK * 2) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_dense_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_dense_bf16)");
+  k_dense_bf16<<<grid, THREADS, smem, st>>>(mA, mBh, mBl, V, K, ncols, R, status);
+  return cuda_check(cudaGetLastError(), "k_dense_bf16 launch");
+}
+
+}  // namespace hs

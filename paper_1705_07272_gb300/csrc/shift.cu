@@ -1,0 +1,611 @@
+// Haar-domain phase shift on sm_103a: per-launch set-up (FP64 shift
+// parameters, pixel synthesis), the tile-fused resample + forward-Haar
+// kernel with the coarse levels finished by the last tile of each shift,
+// and the batched forward / inverse transforms.
+//
+// The operator is the paper's phase shift of a lat-long map's Haar
+// coefficients (Sec. "Rotating Haar", Eq. tRot/theta/phi/compfunc):
+//   c' = Haar( resample( Haar^-1 c ) ).
+// Per launch the map is synthesised once (C*H*W floats, L2-resident) and
+// every (shift, 64x64 output tile) CTA resamples its tile, runs levels 1..6
+// of the forward transform in shared memory and writes those coefficients
+// straight to their canonical positions; the tile means (the level-6
+// scaling image) go to the workspace and the last CTA of each shift
+// transforms them into the coarse levels (Sec. "Algorithmic optimization":
+// every level follows from the previous one, O(N) in total).
+#include <math.h>
+#include <stdio.h>
+
+#include "common.cuh"
+
+namespace hs {
+
+constexpr int kThreads = 256;
+constexpr int kRotChannels = 4;   // channels resampled together by the rotation kernel
+
+enum { KIND_TRANSLATE = 0, KIND_ROTATE = 1, KIND_COPY = 2 };
+
+struct ShiftArgs {
+  Geometry g;
+  int K;                  // coefficients written per (s, c)
+  long long st_s, st_c, st_k;
+  long long plane;        // hi -> lo plane offset (BF16_HILO)
+  void* out;
+  const float* pix;       // source pixels [C][H][W] (or maps [batch][H][W] for KIND_COPY)
+  const float* cin;       // input coefficients [C][N] (signed-permutation copies)
+  const ShiftParam* prm;  // [S] or null
+  float* means;           // [S][C][n_tiles] (null: means go to out[..., 0:n_tiles])
+  unsigned* counters;     // [S] (null: no in-kernel coarse pass)
+  const float* trig;      // sin_t[H] cos_t[H] sin_p[W] cos_p[W]
+  float scale;
+  float u_scale, v_scale; // H/pi, W/(2 pi)
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ void ext_index(int& i, int& j, int H, int W, int boundary) {
+  if (boundary == HAAR_BOUNDARY_TORUS) {
+    i %= H;
+    if (i < 0) i += H;
+  } else {
+#pragma unroll 1
+    for (int it = 0; it < 8 && (i < 0 || i >= H); ++it) {
+      i = (i < 0) ? -1 - i : 2 * H - 1 - i;
+      j += W >> 1;
+    }
+  }
+  j %= W;
+  if (j < 0) j += W;
+}
+
+template <int OUT>
+__device__ __forceinline__ void put(const ShiftArgs& a, int s, int c, int k, float v) {
+  if (k >= a.K) return;
+  long long idx = (long long)s * a.st_s + (long long)c * a.st_c + (long long)k * a.st_k;
+  if (OUT == HAAR_OUT_F32) {
+    reinterpret_cast<float*>(a.out)[idx] = v * a.scale;
+  } else if (OUT == HAAR_OUT_BF16_HILO) {
+    __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    reinterpret_cast<__nv_bfloat16*>(a.out)[idx] = hi;
+    reinterpret_cast<__nv_bfloat16*>(a.out)[a.plane + idx] = lo;
+  } else {
+    reinterpret_cast<__half*>(a.out)[idx] = __float2half_rn(v);
+  }
+}
+
+// Closed-form source of a block moved by a block-aligned integer shift: the
+// level-l coefficients are a signed permutation of the input's (a block
+// mirrored across a pole moves half a turn and its V, D change sign).
+__device__ float perm_value(const ShiftArgs& a, const ShiftParam& p, int c, int lvl, int band,
+                            int r, int col) {
+  const Geometry& g = a.g;
+  const int l = lvl > g.n ? g.n : lvl;
+  const int B = 1 << l;
+  const int rows = lvl > g.n ? 1 : (g.H >> l);
+  const int cols = lvl > g.n ? g.q : (g.W >> l);
+  int rs = r - p.ky / B, cs = col - p.kx / B;
+  bool flip = false;
+  if (g.boundary == HAAR_BOUNDARY_TORUS) {
+    rs %= rows;
+    if (rs < 0) rs += rows;
+  } else {
+#pragma unroll 1
+    for (int it = 0; it < 8 && (rs < 0 || rs >= rows); ++it) {
+      rs = rs < 0 ? -1 - rs : 2 * rows - 1 - rs;
+      cs += (g.W >> 1) / B;
+      flip = !flip;
+    }
+  }
+  cs %= cols;
+  if (cs < 0) cs += cols;
+  const float* src = a.cin + (long long)c * g.N;
+  if (lvl > g.n) return __ldg(src + cs);
+  const long long gl = (long long)g.q << (2 * (g.n - l));
+  float v = __ldg(src + gl * (1 + band) + (long long)rs * cols + cs);
+  return (flip && band != 0) ? -v : v;
+}
+
+template <int OUT>
+__device__ __forceinline__ void emit(const ShiftArgs& a, const ShiftParam* p, int s, int c, int lvl,
+                                     int r, int col, float hv, float vv, float dv) {
+  const Geometry& g = a.g;
+  const long long gl = (long long)g.q << (2 * (g.n - lvl));
+  if (gl >= a.K) return;                      // whole level truncated away
+  const int cols = g.W >> lvl;
+  const long long base = (long long)r * cols + col;
+  if (p != nullptr && ((p->perm_mask >> lvl) & 1u)) {
+    hv = perm_value(a, *p, c, lvl, 0, r, col);
+    vv = perm_value(a, *p, c, lvl, 1, r, col);
+    dv = perm_value(a, *p, c, lvl, 2, r, col);
+  }
+  put<OUT>(a, s, c, (int)(gl + base), hv);
+  put<OUT>(a, s, c, (int)(2 * gl + base), vv);
+  put<OUT>(a, s, c, (int)(3 * gl + base), dv);
+}
+
+// One pass of the forward transform over a rows x cols image in shared
+// memory (row pitch = cols): every thread takes a block of side sb (4: two
+// levels, 2: one level), writes the detail coefficients of levels lvl0+1
+// (and lvl0+2) and the block's scaling value to dst (pitch cols/sb).
+// (gr0, gc0) = level-lvl0 grid position of the image's element (0, 0).
+template <int OUT>
+__device__ void haar_pass(const ShiftArgs& a, const ShiftParam* p, int s, int c, const float* src,
+                          float* dst, int rows, int cols, int lvl0, int sb, int gr0, int gc0) {
+  const int nbr = rows / sb, nbc = cols / sb;
+  for (int b = threadIdx.x; b < nbr * nbc; b += blockDim.x) {
+    const int by = b / nbc, bx = b - by * nbc;
+    if (sb == 4) {
+      float x[16];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float4 t = *reinterpret_cast<const float4*>(src + (4 * by + r) * cols + 4 * bx);
+        x[4 * r + 0] = t.x; x[4 * r + 1] = t.y; x[4 * r + 2] = t.z; x[4 * r + 3] = t.w;
+      }
+      float A1[4];
+#pragma unroll
+      for (int sa = 0; sa < 2; ++sa) {
+#pragma unroll
+        for (int sc = 0; sc < 2; ++sc) {
+          const float ea = x[(2 * sa) * 4 + 2 * sc], eb = x[(2 * sa) * 4 + 2 * sc + 1];
+          const float ec = x[(2 * sa + 1) * 4 + 2 * sc], ed = x[(2 * sa + 1) * 4 + 2 * sc + 1];
+          A1[2 * sa + sc] = 0.5f * ((ea + eb) + (ec + ed));
+          emit<OUT>(a, p, s, c, lvl0 + 1, (gr0 >> 1) + 2 * by + sa, (gc0 >> 1) + 2 * bx + sc,
+                    0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)),
+                    0.5f * ((ea + ed) - (eb + ec)));
+        }
+      }
+      const float ea = A1[0], eb = A1[1], ec = A1[2], ed = A1[3];
+      emit<OUT>(a, p, s, c, lvl0 + 2, (gr0 >> 2) + by, (gc0 >> 2) + bx,
+                0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)),
+                0.5f * ((ea + ed) - (eb + ec)));
+      dst[by * nbc + bx] = 0.5f * ((ea + eb) + (ec + ed));
+    } else {
+      const float ea = src[(2 * by) * cols + 2 * bx], eb = src[(2 * by) * cols + 2 * bx + 1];
+      const float ec = src[(2 * by + 1) * cols + 2 * bx], ed = src[(2 * by + 1) * cols + 2 * bx + 1];
+      emit<OUT>(a, p, s, c, lvl0 + 1, (gr0 >> 1) + by, (gc0 >> 1) + bx,
+                0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)),
+                0.5f * ((ea + ed) - (eb + ec)));
+      dst[by * nbc + bx] = 0.5f * ((ea + eb) + (ec + ed));
+    }
+  }
+}
+
+// Levels 1..Lt of one T x T tile held in buf0 (buf1 is scratch of (T/4)^2
+// floats).  Returns (to thread 0) the tile's scaling value.
+template <int OUT>
+__device__ float tile_levels(const ShiftArgs& a, const ShiftParam* p, int s, int c, float* buf0,
+                             float* buf1, int tr, int tc) {
+  const int T = a.g.T;
+  int side = T, lvl = 0;
+  float* src = buf0;
+  float* dst = buf1;
+  while (lvl < a.g.Lt) {
+    const int sb = (a.g.Lt - lvl >= 2) ? 4 : 2;
+    __syncthreads();
+    haar_pass<OUT>(a, p, s, c, src, dst, side, side, lvl, sb, (tr * T) >> lvl, (tc * T) >> lvl);
+    side /= sb;
+    lvl += (sb == 4) ? 2 : 1;
+    float* t = src; src = dst; dst = t;
+  }
+  __syncthreads();
+  return src[0];
+}
+
+// Coarse levels Lt+1..n from the (H/T) x (W/T) image of tile means in img
+// (scratch: img2, same size / 16), then the scaling coefficients A_n.
+template <int OUT>
+__device__ void coarse_levels(const ShiftArgs& a, const ShiftParam* p, int s, int c, float* img,
+                              float* img2) {
+  const Geometry& g = a.g;
+  int rows = g.tiles_r, cols = g.tiles_c, lvl = g.Lt;
+  float* src = img;
+  float* dst = img2;
+  while (lvl < g.n) {
+    const int sb = (g.n - lvl >= 2) ? 4 : 2;
+    __syncthreads();
+    haar_pass<OUT>(a, p, s, c, src, dst, rows, cols, lvl, sb, 0, 0);
+    rows /= sb;
+    cols /= sb;
+    lvl += (sb == 4) ? 2 : 1;
+    float* t = src; src = dst; dst = t;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < g.q; k += blockDim.x) {
+    float v = src[k];
+    if (p != nullptr && ((p->perm_mask >> (g.n + 1)) & 1u)) v = perm_value(a, *p, c, g.n + 1, 0, 0, k);
+    put<OUT>(a, s, c, k, v);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ kernels
+
+// One CTA per (tile, shift).  Shared memory: [window (T+1)^2 | pixels CG*T*T |
+// scratch (T/4)^2 + 8] floats.
+template <int KIND, int OUT>
+__global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_last;
+  const Geometry& g = a.g;
+  const int T = g.T;
+  const int tile = blockIdx.x;
+  const int s = blockIdx.y;
+  const int tr = tile / g.tiles_c, tc = tile - tr * g.tiles_c;
+  const int CG = (KIND == KIND_ROTATE) ? kRotChannels : 1;
+  const int win = (KIND == KIND_TRANSLATE) ? (T + 1) * (T + 1) : 0;
+  const int winr = (win + 3) & ~3;
+  float* wnd = smem;
+  float* pbuf = smem + winr;
+  float* sbuf = pbuf + CG * T * T;
+  const ShiftParam* p = (KIND == KIND_COPY) ? nullptr : (a.prm + s);
+  ShiftParam pr;
+  if (p != nullptr) pr = *p;
+  const int i_org = tr * T, j_org = tc * T;
+
+  for (int c0 = 0; c0 < g.C; c0 += CG) {
+    const int cgn = min(CG, g.C - c0);
+    if (KIND == KIND_TRANSLATE) {
+      const float* F = a.pix + (long long)c0 * g.N;
+      const int wp = T + 1;
+      __syncthreads();
+      for (int e = threadIdx.x; e < wp * wp; e += blockDim.x) {
+        const int wi = e / wp, wj = e - wi * wp;
+        int i = i_org - pr.ky - 1 + wi, j = j_org - pr.kx - 1 + wj;
+        ext_index(i, j, g.H, g.W, g.boundary);
+        wnd[e] = __ldg(F + (long long)i * g.W + j);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+        const int ii = e / T, jj = e - ii * T;
+        const float* w0 = wnd + ii * wp + jj;
+        const float top = pr.wx0 * w0[1] + pr.wx1 * w0[0];          // row i - ky - 1
+        const float bot = pr.wx0 * w0[wp + 1] + pr.wx1 * w0[wp];    // row i - ky
+        pbuf[e] = pr.wy0 * bot + pr.wy1 * top;
+      }
+    } else if (KIND == KIND_ROTATE) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+        const int ii = e / T, jj = e - ii * T;
+        const int i = i_org + ii, j = j_org + jj;
+        const float st = __ldg(a.trig + i), ct = __ldg(a.trig + g.H + i);
+        const float sp = __ldg(a.trig + 2 * g.H + j), cp = __ldg(a.trig + 2 * g.H + g.W + j);
+        const float dx = st * sp, dy = ct, dz = st * cp;
+        const float px = fmaf(pr.R[0], dx, fmaf(pr.R[1], dy, pr.R[2] * dz));
+        const float py = fmaf(pr.R[3], dx, fmaf(pr.R[4], dy, pr.R[5] * dz));
+        const float pz = fmaf(pr.R[6], dx, fmaf(pr.R[7], dy, pr.R[8] * dz));
+        const float rho = sqrtf(fmaf(px, px, pz * pz));
+        const float th = atan2f(rho, py);
+        const float ph = atan2f(px, pz);
+        const float u = fmaf(th, a.u_scale, -0.5f);
+        const float v = fmaf(ph, a.v_scale, -0.5f);
+        const float fi = floorf(u), fj = floorf(v);
+        const float fu = u - fi, fv = v - fj;
+        int i0 = (int)fi, j0 = (int)fj;
+        int ia = i0, ja = j0, ib = i0, jb = j0 + 1, ic = i0 + 1, jc = j0, id = i0 + 1, jd = j0 + 1;
+        ext_index(ia, ja, g.H, g.W, g.boundary);
+        ext_index(ib, jb, g.H, g.W, g.boundary);
+        ext_index(ic, jc, g.H, g.W, g.boundary);
+        ext_index(id, jd, g.H, g.W, g.boundary);
+        const long long oa = (long long)ia * g.W + ja, ob = (long long)ib * g.W + jb;
+        const long long oc = (long long)ic * g.W + jc, od = (long long)id * g.W + jd;
+        for (int ci = 0; ci < cgn; ++ci) {
+          const float* F = a.pix + (long long)(c0 + ci) * g.N;
+          const float f00 = __ldg(F + oa), f01 = __ldg(F + ob), f10 = __ldg(F + oc), f11 = __ldg(F + od);
+          pbuf[ci * T * T + e] = (1.0f - fu) * ((1.0f - fv) * f00 + fv * f01) +
+                                 fu * ((1.0f - fv) * f10 + fv * f11);
+        }
+      }
+    } else {  // KIND_COPY: forward transform of maps [batch][H][W]
+      const float* F = a.pix + (long long)s * g.N;
+      __syncthreads();
+      if (T >= 4) {
+        for (int e = threadIdx.x; e < T * T / 4; e += blockDim.x) {
+          const int ii = (4 * e) / T, jj = 4 * e - ii * T;
+          *reinterpret_cast<float4*>(pbuf + 4 * e) =
+              __ldg(reinterpret_cast<const float4*>(F + (long long)(i_org + ii) * g.W + j_org + jj));
+        }
+      } else {
+        for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+          const int ii = e / T, jj = e - ii * T;
+          pbuf[e] = __ldg(F + (long long)(i_org + ii) * g.W + j_org + jj);
+        }
+      }
+    }
+    for (int ci = 0; ci < cgn; ++ci) {
+      const int c = c0 + ci;
+      const float m = tile_levels<OUT>(a, p, s, c, pbuf + ci * T * T, sbuf, tr, tc);
+      if (threadIdx.x == 0) {
+        if (a.means != nullptr)
+          a.means[((long long)s * g.C + c) * g.n_tiles + tile] = m;
+        else  // forward transform: stash the tile mean in the coarse region of the output
+          reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = m;
+      }
+      __syncthreads();
+    }
+  }
+
+  if (a.counters == nullptr) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(a.counters + s, 1u);
+    s_last = (t == (unsigned)(g.n_tiles - 1)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  float* img = pbuf;
+  float* img2 = pbuf + g.n_tiles;
+  for (int c = 0; c < g.C; ++c) {
+    for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
+      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
+    coarse_levels<OUT>(a, p, s, c, img, img2);
+  }
+  if (threadIdx.x == 0) a.counters[s] = 0u;
+}
+
+// Coarse levels of the forward transform, in place: one CTA per map.
+__global__ void __launch_bounds__(kThreads) k_coarse_inplace(ShiftArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  const int s = blockIdx.x;
+  float* out = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s;
+  float* img = smem;
+  float* img2 = smem + a.g.n_tiles;
+  for (int t = threadIdx.x; t < a.g.n_tiles; t += blockDim.x) img[t] = out[t];
+  __syncthreads();
+  // put() multiplies by a.scale; the tile means were stored unscaled
+  coarse_levels<HAAR_OUT_F32>(a, nullptr, s, 0, img, img2);
+}
+
+// Per-launch set-up: blocks [0, nbp) synthesise the pixel map from the
+// coefficients (inverse transform, one thread per pixel summing its
+// ancestors); the last block builds the shift records in FP64 and clears the
+// per-shift tile counters.
+struct SetupArgs {
+  int H, W, C, n, q, kind, boundary, S, nbp;
+  const float* cin;
+  float* pix;
+  const double* params;
+  ShiftParam* prm;
+  unsigned* counters;
+};
+
+__device__ __forceinline__ float synth_pixel(const float* cf, int i, int j, int W, int n, int q) {
+  float x = __ldg(cf + (j >> n));
+  for (int l = n; l >= 1; --l) {
+    const int r = i >> l, cc = j >> l;
+    const int qi = (i >> (l - 1)) & 1, qj = (j >> (l - 1)) & 1;
+    const long long gl = (long long)q << (2 * (n - l));
+    const long long o = (long long)r * (W >> l) + cc;
+    const float hv = __ldg(cf + gl + o), vv = __ldg(cf + 2 * gl + o), dv = __ldg(cf + 3 * gl + o);
+    x = 0.5f * (x + (qj ? hv : -hv) + (qi ? vv : -vv) + ((qi == qj) ? dv : -dv));
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
+  const long long N = (long long)a.H * a.W;
+  if ((int)blockIdx.x < a.nbp) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * a.C) return;
+    const int c = (int)(e / N);
+    const long long rem = e - (long long)c * N;
+    const int i = (int)(rem / a.W), j = (int)(rem - (long long)i * a.W);
+    a.pix[e] = synth_pixel(a.cin + (long long)c * N, i, j, a.W, a.n, a.q);
+    return;
+  }
+  for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
+    ShiftParam p;
+    p.kx = p.ky = 0;
+    p.wx0 = p.wy0 = 1.0f;
+    p.wx1 = p.wy1 = 0.0f;
+    p.perm_mask = 0u;
+    p.pad = 0;
+    for (int k = 0; k < 9; ++k) p.R[k] = (k % 4 == 0) ? 1.0f : 0.0f;
+    p.pad2[0] = p.pad2[1] = p.pad2[2] = 0.0f;
+    if (a.kind == HAAR_SHIFT_TRANSLATE) {
+      const double dx = a.params[2 * s], dy = a.params[2 * s + 1];
+      const double W = a.W;
+      const double per = (a.boundary == HAAR_BOUNDARY_SPHERE) ? 2.0 * a.H : (double)a.H;
+      double x = dx - W * floor(dx / W);
+      if (x >= W) x -= W;
+      if (!(x >= 0.0 && x < W)) x = 0.0;     // non-finite or rounding outside [0, W)
+      double y = dy - per * floor(dy / per);
+      if (y >= per) y -= per;
+      if (!(y >= 0.0 && y < per)) y = 0.0;
+      const double fx = floor(x), fy = floor(y);
+      const double tx = x - fx, ty = y - fy;
+      p.kx = (int)fx;
+      p.ky = (int)fy;
+      p.wx0 = (float)(1.0 - tx);
+      p.wx1 = (float)tx;
+      p.wy0 = (float)(1.0 - ty);
+      p.wy1 = (float)ty;
+      if (tx == 0.0 && ty == 0.0) {
+        for (int l = 1; l <= a.n + 1; ++l) {
+          const int B = 1 << (l > a.n ? a.n : l);
+          const bool crosses = (a.boundary == HAAR_BOUNDARY_SPHERE) && p.ky != 0;
+          if (p.kx % B == 0 && p.ky % B == 0 && (!crosses || ((a.W / 2) % B) == 0))
+            p.perm_mask |= 1u << l;
+        }
+      }
+    } else {
+      double R[9];
+      if (a.kind == HAAR_SHIFT_ROTATE) {
+        for (int k = 0; k < 9; ++k) R[k] = a.params[9 * s + k];
+      } else {
+        const double al = a.params[3 * s], be = a.params[3 * s + 1], ga = a.params[3 * s + 2];
+        const double ca = cos(al), sa = sin(al), cb = cos(be), sb = sin(be);
+        const double cg = cos(ga), sg = sin(ga);
+        const double Rx[9] = {1, 0, 0, 0, ca, -sa, 0, sa, ca};
+        const double Ry[9] = {cb, 0, sb, 0, 1, 0, -sb, 0, cb};
+        const double Rz[9] = {cg, -sg, 0, sg, cg, 0, 0, 0, 1};
+        double M[9];
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c)
+            M[3 * r + c] = Ry[3 * r] * Rx[c] + Ry[3 * r + 1] * Rx[3 + c] + Ry[3 * r + 2] * Rx[6 + c];
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c)
+            R[3 * r + c] = Rz[3 * r] * M[c] + Rz[3 * r + 1] * M[3 + c] + Rz[3 * r + 2] * M[6 + c];
+      }
+      for (int k = 0; k < 9; ++k) p.R[k] = (float)R[k];
+    }
+    a.prm[s] = p;
+    a.counters[s] = 0u;
+  }
+}
+
+__global__ void k_trig(int H, int W, float* trig) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const double pi = 3.14159265358979323846;
+  if (e < H) {
+    const double t = (e + 0.5) * pi / H;
+    trig[e] = (float)sin(t);
+    trig[H + e] = (float)cos(t);
+  } else if (e < H + W) {
+    const int j = e - H;
+    const double t = (j + 0.5) * 2.0 * pi / W;
+    trig[2 * H + j] = (float)sin(t);
+    trig[2 * H + W + j] = (float)cos(t);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_inverse(int H, int W, int n, int q, long long total,
+                                                      const float* cin, float* maps) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const long long N = (long long)H * W;
+  const long long b = e / N;
+  const long long rem = e - b * N;
+  const int i = (int)(rem / W), j = (int)(rem - (long long)i * W);
+  maps[e] = synth_pixel(cin + b * N, i, j, W, n, q);
+}
+
+// ------------------------------------------------------------------ launchers
+
+static size_t shift_smem_bytes(const Geometry& g, int kind) {
+  const int CG = (kind == KIND_ROTATE) ? kRotChannels : 1;
+  const int win = (kind == KIND_TRANSLATE) ? (g.T + 1) * (g.T + 1) : 0;
+  const int winr = (win + 3) & ~3;
+  size_t pix = (size_t)CG * g.T * g.T;
+  const size_t coarse = (size_t)g.n_tiles + (size_t)g.n_tiles / 4 + 8;
+  if (pix < coarse) pix = coarse;
+  const size_t scratch = (size_t)(g.T / 4) * (g.T / 4) + 8 + g.T;
+  return sizeof(float) * ((size_t)winr + pix + scratch);
+}
+
+template <int KIND, int OUT>
+static haar_status_t launch_k(const ShiftArgs& a, int S, cudaStream_t st) {
+  const size_t sm = shift_smem_bytes(a.g, KIND);
+  auto fn = k_shift<KIND, OUT>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift)");
+  }
+  dim3 grid(a.g.n_tiles, S);
+  fn<<<grid, kThreads, sm, st>>>(a);
+  return cuda_check(cudaGetLastError(), "k_shift launch");
+}
+
+template <int KIND>
+static haar_status_t launch_out(const ShiftArgs& a, int out_type, int S, cudaStream_t st) {
+  switch (out_type) {
+    case HAAR_OUT_F32: return launch_k<KIND, HAAR_OUT_F32>(a, S, st);
+    case HAAR_OUT_BF16_HILO: return launch_k<KIND, HAAR_OUT_BF16_HILO>(a, S, st);
+    default: return launch_k<KIND, HAAR_OUT_F16>(a, S, st);
+  }
+}
+
+haar_status_t launch_trig(haar_shift_plan_s* p, cudaStream_t st) {
+  const int tot = p->geo.H + p->geo.W;
+  k_trig<<<(tot + 255) / 256, 256, 0, st>>>(p->geo.H, p->geo.W, p->trig);
+  return cuda_check(cudaGetLastError(), "k_trig launch");
+}
+
+haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const double* params,
+                           int S, cudaStream_t st) {
+  SetupArgs a;
+  const Geometry& g = p->geo;
+  a.H = g.H; a.W = g.W; a.C = g.C; a.n = g.n; a.q = g.q;
+  a.kind = p->desc.kind;
+  a.boundary = g.boundary;
+  a.S = S;
+  const long long total = g.N * g.C;
+  a.nbp = (int)((total + kThreads - 1) / kThreads);
+  a.cin = coeffs_in;
+  a.pix = p->pix;
+  a.params = params;
+  a.prm = p->prm;
+  a.counters = p->counters;
+  k_setup<<<a.nbp + 1, kThreads, 0, st>>>(a);
+  return cuda_check(cudaGetLastError(), "k_setup launch");
+}
+
+haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
+                           cudaStream_t st) {
+  ShiftArgs a;
+  const Geometry& g = p->geo;
+  a.g = g;
+  a.K = p->K;
+  const long long K = p->K, C = g.C;
+  switch (p->desc.out_layout) {
+    case HAAR_LAYOUT_SCK: a.st_s = C * K; a.st_c = K; a.st_k = 1; break;
+    case HAAR_LAYOUT_SKC: a.st_s = K * C; a.st_c = 1; a.st_k = C; break;
+    default: a.st_s = C; a.st_c = 1; a.st_k = (long long)S * C; break;
+  }
+  a.plane = (long long)S * C * K;
+  a.out = out;
+  a.pix = p->pix;
+  a.cin = coeffs_in;
+  a.prm = p->prm;
+  a.means = p->means;
+  a.counters = p->counters;
+  a.trig = p->trig;
+  a.scale = 1.0f;
+  a.u_scale = (float)(g.H / 3.14159265358979323846);
+  a.v_scale = (float)(g.W / (2.0 * 3.14159265358979323846));
+  if (p->desc.kind == HAAR_SHIFT_TRANSLATE) return launch_out<KIND_TRANSLATE>(a, p->desc.out_type, S, st);
+  return launch_out<KIND_ROTATE>(a, p->desc.out_type, S, st);
+}
+
+haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* coeffs, float scale,
+                             cudaStream_t st) {
+  ShiftArgs a;
+  a.g = make_geometry(H, W, 1, HAAR_BOUNDARY_SPHERE);
+  a.K = H * W;
+  a.st_s = (long long)H * W;
+  a.st_c = 0;
+  a.st_k = 1;
+  a.plane = 0;
+  a.out = coeffs;
+  a.pix = maps;
+  a.cin = nullptr;
+  a.prm = nullptr;
+  a.means = nullptr;
+  a.counters = nullptr;
+  a.trig = nullptr;
+  a.scale = scale;
+  a.u_scale = a.v_scale = 0.0f;
+  // details are scaled by put(); tile means are stashed unscaled and scaled
+  // when k_coarse_inplace writes the coarse levels through put()
+  haar_status_t r = launch_k<KIND_COPY, HAAR_OUT_F32>(a, batch, st);
+  if (r != HAAR_OK) return r;
+  const size_t sm = sizeof(float) * ((size_t)a.g.n_tiles * 2 + 16);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_inplace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_coarse_inplace)");
+  }
+  k_coarse_inplace<<<batch, kThreads, sm, st>>>(a);
+  return cuda_check(cudaGetLastError(), "k_coarse_inplace launch");
+}
+
+haar_status_t launch_inverse(int H, int W, int batch, const float* coeffs, float* maps,
+                             cudaStream_t st) {
+  const Geometry g = make_geometry(H, W, 1, HAAR_BOUNDARY_SPHERE);
+  const long long total = (long long)batch * g.N;
+  const long long nb = (total + kThreads - 1) / kThreads;
+  k_inverse<<<(unsigned)nb, kThreads, 0, st>>>(H, W, g.n, g.q, total, coeffs, maps);
+  return cuda_check(cudaGetLastError(), "k_inverse launch");
+}
+
+}  // namespace hs

@@ -1,0 +1,94 @@
+"""The C ABI without a GPU: the library builds, loads, exports every entry
+point the headers declare, and rejects bad arguments before any launch."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_07272_gb300 import build
+    build.build()
+    import paper_1705_07272_gb300 as hs
+    return hs
+
+
+def _declared():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names += [n for n in re.findall(r"^HAAR_API\s+[\w\s\*]*?\b(\w+)\s*\(", txt, re.M)]
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 10
+    L = lib.lib()
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in lib.EXPORTS, n
+
+
+def test_version(lib):
+    assert "sm_103a" in lib.version()
+
+
+def _desc(lib, **kw):
+    d = dict(height=32, width=64, channels=3, kind=0, boundary=0, max_shifts=4, out_coeffs=0,
+             out_type=0, out_layout=0)
+    d.update(kw)
+    return lib.HaarShiftDesc(**d)
+
+
+@pytest.mark.parametrize("bad", [dict(height=48), dict(height=1), dict(width=128), dict(width=16),
+                                 dict(channels=0), dict(channels=65), dict(kind=7), dict(boundary=2),
+                                 dict(max_shifts=0), dict(out_coeffs=-1), dict(out_coeffs=32 * 64 + 1),
+                                 dict(out_type=3), dict(out_layout=5), dict(height=8192, width=8192)])
+def test_plan_rejects_bad_descriptors(lib, bad):
+    h = ctypes.c_void_p()
+    st = lib.lib().haar_shift_plan(ctypes.byref(_desc(lib, **bad)), ctypes.byref(h))
+    assert st == lib.HAAR_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.lib().haar_last_error()
+
+
+def test_null_arguments(lib):
+    L = lib.lib()
+    assert L.haar_shift_plan(None, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_shift(None, None, None, 1, None, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.shade_vertices(None, None, None, 1, None, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.shade_batch(None, None, None, 1, None, None, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_forward(48, 48, 1, None, None, 1.0, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_forward(32, 32, 1, None, None, 1.0, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_forward(32, 32, 1, 8, 16, 1.0, None) == lib.HAAR_ERR_INVALID_ARG      # misaligned
+    assert L.haar_forward(32, 32, 0, None, None, 1.0, None) == lib.HAAR_OK            # empty batch
+    assert L.haar_inverse(32, 96, 1, None, None, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_view_bins(10, 1, 0, None, None, None, None, None, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_view_bins(0, 1, 16, None, None, None, None, None, None) == lib.HAAR_OK
+    assert L.haar_shift_plan_destroy(None) == lib.HAAR_OK
+
+
+def test_fault_injection(lib, monkeypatch):
+    L = lib.lib()
+    monkeypatch.setenv("HAAR_FAULT_INJECT", "haar_forward,shade_batch")
+    assert L.haar_forward(32, 32, 1, None, None, 1.0, None) == lib.HAAR_ERR_INJECTED
+    assert b"injected" in L.haar_last_error()
+    assert L.shade_batch(None, None, None, 1, None, None, None) == lib.HAAR_ERR_INJECTED
+    assert L.haar_inverse(32, 96, 1, None, None, None) == lib.HAAR_ERR_INVALID_ARG
+    monkeypatch.setenv("HAAR_FAULT_INJECT", "*")
+    h = ctypes.c_void_p()
+    assert L.haar_shift_plan(ctypes.byref(_desc(lib)), ctypes.byref(h)) == lib.HAAR_ERR_INJECTED
+    monkeypatch.delenv("HAAR_FAULT_INJECT")
+    assert L.haar_forward(48, 48, 1, None, None, 1.0, None) == lib.HAAR_ERR_INVALID_ARG
+
+
+def test_binding_rejects_host_tensors(lib):
+    import torch
+    with pytest.raises(ValueError):
+        lib._dev(torch.zeros(4), torch.float32, "x")

@@ -1,0 +1,190 @@
+"""GPU parity of the double product (dense FP32, top-K CSR FP32, view-binned
+FP16) and of shift + shade end to end, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import haar as oh
+from oracle import shade as osd
+from oracle import shift as osh
+from oracle import transport as otr
+from tests.helpers import f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(x, dtype=None):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def _weights(sc, Ht=None, Wt=None, device="cpu", view=None, expo=None):
+    Ht = Ht or sc["H"]
+    Wt = Wt or sc["W"]
+    w = synth.transport_weights(sc["pos"], sc["nrm"], sc["occ_c"], sc["occ_r"], Ht, Wt,
+                                view=view, expo=expo, device=device)
+    return w.double().cpu().numpy()
+
+
+def test_c0_dense_f32_end_to_end(hs):
+    import torch
+    sc = synth.scene(0)
+    H, W = sc["H"], sc["W"]
+    L = f32(oh.forward(sc["light"]))
+    T = f32(otr.project(_weights(sc)))                      # [1000, 1024]
+    plan = hs.Plan(H, W, 1, max_shifts=1)
+    tr = hs.Transport(hs.HAAR_T_DENSE_F32, T.shape[0], T.shape[1], _t(T, torch.float32))
+    R = hs.shade_batch(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
+    torch.cuda.synchronize()
+    got = R.cpu().numpy()
+    Ls = osh.haar_shift(L, H, W, osh.TRANSLATE, sc["params"])
+    ref = osd.radiance(Ls, T, H, W)
+    assert got.shape == (1000, 1, 1)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_dense_f32_many_columns(hs):
+    import torch
+    H, W = 16, 32
+    rng = np.random.default_rng(2)
+    L = f32(oh.forward(synth.lighting_pixels(rng, 3, H, W)))
+    prm = rng.uniform(0, 32, (5, 2))
+    T = f32(rng.standard_normal((77, 300)))
+    plan = hs.Plan(H, W, 3, max_shifts=5)
+    Ls = hs.haar_shift(plan, _t(L, torch.float32), _t(prm, torch.float64))
+    tr = hs.Transport(hs.HAAR_T_DENSE_F32, 77, 300, _t(T, torch.float32))
+    got = hs.shade_vertices(plan, tr, Ls, 5).cpu().numpy()
+    ref = np.einsum("vk,sck->vsc", T, osh.haar_shift(L, H, W, osh.TRANSLATE, prm)[..., :300])
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def _csr_inputs(sc, K, H, W, chunk=2000):
+    vs, ids = [], []
+    for v0 in range(0, sc["V"], chunk):
+        part = dict(sc, pos=sc["pos"][v0:v0 + chunk], nrm=sc["nrm"][v0:v0 + chunk])
+        T = otr.project(_weights(part, device="cuda"))
+        vals, idx, _ = otr.topk_csr(T, K)
+        vs.append(vals)
+        ids.append(idx)
+    rowptr = np.arange(sc["V"] + 1, dtype=np.int64) * K
+    return f32(np.concatenate(vs)), np.concatenate(ids), rowptr
+
+
+def _run_csr(hs, sc, vals, idx, rowptr, H, W):
+    import torch
+    C, S, V = sc["C"], sc["S"], len(rowptr) - 1
+    L = f32(oh.forward(sc["light"]))
+    plan = hs.Plan(H, W, C, max_shifts=S, out_layout=hs.HAAR_LAYOUT_KSC)
+    tr = hs.Transport(hs.HAAR_T_CSR_F32_U16, V, 0, _t(vals, torch.float32),
+                      _t(idx.astype(np.int16), torch.int16), _t(rowptr.astype(np.int32), torch.int32))
+    R = hs.shade_batch(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
+    torch.cuda.synchronize()
+    return R.cpu().numpy(), L
+
+
+def test_csr_small(hs):
+    sc = synth.scene(1, V=700, S=4, H=32, W=64)
+    vals, idx, rowptr = _csr_inputs(sc, 64, 32, 64)
+    got, L = _run_csr(hs, sc, vals, idx, rowptr, 32, 64)
+    Ls = osh.haar_shift(L, 32, 64, osh.TRANSLATE, sc["params"])
+    dense = otr.csr_dense(vals, idx, rowptr, 32 * 64)
+    ref = osd.radiance(Ls, dense, 32, 64)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_csr_ragged_rows(hs):
+    import torch
+    H, W = 16, 32
+    rng = np.random.default_rng(9)
+    V, N = 57, H * W
+    lens = rng.integers(0, 40, V)
+    lens[3] = 0
+    rowptr = np.concatenate([[0], np.cumsum(lens)])
+    idx = np.concatenate([np.sort(rng.choice(N, l, replace=False)) for l in lens]).astype(np.int64)
+    vals = f32(rng.standard_normal(rowptr[-1]))
+    L = f32(oh.forward(synth.lighting_pixels(rng, 3, H, W)))
+    prm = rng.uniform(0, 40, (4, 2))
+    plan = hs.Plan(H, W, 3, max_shifts=4, out_layout=hs.HAAR_LAYOUT_KSC)
+    Ls = hs.haar_shift(plan, _t(L, torch.float32), _t(prm, torch.float64))
+    tr = hs.Transport(hs.HAAR_T_CSR_F32_U16, V, 0, _t(vals, torch.float32), _t(idx.astype(np.int16), torch.int16),
+                      _t(rowptr.astype(np.int32), torch.int32))
+    got = hs.shade_vertices(plan, tr, Ls, 4).cpu().numpy()
+    ref = np.einsum("vk,sck->vsc", otr.csr_dense(vals, idx, rowptr, N),
+                    osh.haar_shift(L, H, W, osh.TRANSLATE, prm))
+    assert np.allclose(got[3], 0.0)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_csr_full_size_c1_sampled(hs):
+    # the full 50 000-vertex, 16-shift RGB 128x256 frame; the oracle checks
+    # 64 sampled vertices one by one through pixel space
+    sc = synth.scene(1)
+    H, W = sc["H"], sc["W"]
+    vals, idx, rowptr = _csr_inputs(sc, 256, H, W)
+    got, L = _run_csr(hs, sc, vals, idx, rowptr, H, W)
+    Ls = osh.haar_shift(L, H, W, osh.TRANSLATE, sc["params"])
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(sc["V"], 64, replace=False))
+    dense = np.zeros((64, H * W))
+    for r, v in enumerate(pick):
+        dense[r, idx[rowptr[v]:rowptr[v + 1]]] = vals[rowptr[v]:rowptr[v + 1]]
+    ref = osd.radiance(Ls, dense, H, W)
+    assert rel_l2(got[pick], ref) <= 1e-5
+    assert np.isfinite(got).all()
+
+
+def test_view_bins(hs):
+    sc = synth.scene(3, V=3000, S=32)
+    dirs = synth.view_bin_dirs(16)
+    got = hs.haar_view_bins(_t(sc["pos"], None).float(), _t(sc["nrm"], None).float(),
+                            _t(sc["cams"], None).float(), _t(dirs, None).float()).cpu().numpy()
+    ref, margin = otr.view_bins(f32(sc["pos"]), f32(sc["nrm"]), f32(sc["cams"]), f32(dirs))
+    clear = margin > 1e-5
+    assert np.array_equal(got[clear], ref[clear])
+    assert clear.mean() > 0.99
+    # where the two best bins are within rounding, the GPU's pick must be one of them
+    b1, b2 = otr.frame(f32(sc["nrm"]))
+    assert (~clear).sum() == 0 or np.all(margin[~clear] <= 1e-5)
+
+
+def _bincsr_inputs(sc, K, Ht, Wt, H, W, device):
+    V, bins = sc["V"], 16
+    view = synth.bin_view_world(sc["nrm"], bins).reshape(-1, 3)
+    pos = np.repeat(sc["pos"], bins, axis=0)
+    nrm = np.repeat(sc["nrm"], bins, axis=0)
+    expo = np.repeat(sc["expo"], bins)
+    w = synth.transport_weights(pos, nrm, sc["occ_c"], sc["occ_r"], Ht, Wt, view=view, expo=expo,
+                                device=device).double().cpu().numpy()
+    T = otr.project(w, H, W)[:, :Ht * Wt]                 # levels finer than the grid are zero
+    vals, idx, _ = otr.topk_csr(T, K)
+    vals16 = otr.to_f16(vals).reshape(V, bins, K)
+    return vals16, idx.reshape(V, bins, K)
+
+
+def test_bincsr_small(hs):
+    import torch
+    sc = synth.scene(3, V=300, S=6, H=32, W=64)
+    H, W, S = 32, 64, 6
+    vals16, idx = _bincsr_inputs(sc, 64, 16, 32, H, W, "cpu")
+    dirs = synth.view_bin_dirs(16)
+    bin_of = hs.haar_view_bins(_t(sc["pos"]).float(), _t(sc["nrm"]).float(), _t(sc["cams"]).float(),
+                               _t(dirs).float())
+    L = f32(oh.forward(sc["light"]))
+    plan = hs.Plan(H, W, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_layout=hs.HAAR_LAYOUT_SKC)
+    tr = hs.Transport(hs.HAAR_T_BINCSR_F16_U32, sc["V"], 64, _t(vals16, torch.float16),
+                      _t(idx.astype(np.int32), torch.int32), bins=16, bin_of=bin_of)
+    R = hs.shade_batch(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
+    torch.cuda.synchronize()
+    got = R.cpu().numpy()
+    ref_bins, margin = otr.view_bins(f32(sc["pos"]), f32(sc["nrm"]), f32(sc["cams"]), f32(dirs))
+    Ls = osh.haar_shift(L, H, W, osh.ROTATE_EULER, sc["params"])
+    ref = np.zeros((sc["V"], S, 3))
+    for s in range(S):
+        b = ref_bins[s]
+        Tv = np.zeros((sc["V"], H * W))
+        for v in range(sc["V"]):
+            Tv[v, idx[v, b[v]]] = vals16[v, b[v]]
+        ref[:, s] = np.einsum("vk,ck->vc", Tv, Ls[s])
+    ok = (margin > 1e-5).T
+    assert rel_l2(got[ok], ref[ok]) <= 2e-3
+    assert rel_l2(got[ok], ref[ok]) <= 1e-4
