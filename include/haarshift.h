@@ -187,6 +187,68 @@ HAAR_API haar_status_t haar_view_bins(int V, int S, int bins, const float* pos, 
                              const float* cams, const float* bin_dirs, uint8_t* bin_of,
                              void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Transport surrogate (not in the paper; a learned stand-in for stored
+ * transport).  A 4 x 256 GELU MLP maps a vertex's position, normal and view
+ * direction to its transport coefficients at a fixed set of 512 canonical
+ * indices (standardised: T_j = mu_j + sigma_j out_j).  Encoding of the 9
+ * inputs: x, sin(w_f x), cos(w_f x) with w_f = pi 2^(f/2), f = 0..15, zero-padded
+ * to 320.  Flat FP32 parameter vector (haar_mlp_param_count() floats):
+ * W1[256][320] b1[256] W2[256][256] b2 W3 b3 W4 b4 Wo[512][256] bo[512].
+ * Forward and backward run as bf16 tcgen05 GEMMs with FP32 accumulation;
+ * master weights and Adam state are FP32.  A surrogate owns its device
+ * buffers (allocated by haar_mlp_create); compute calls allocate nothing and
+ * calls on one surrogate must be ordered.
+ * ------------------------------------------------------------------------- */
+typedef struct haar_mlp_s* haar_mlp_t;
+
+/* Number of floats in the flat parameter vector. */
+HAAR_API long long haar_mlp_param_count(void);
+
+/* Create a surrogate: training batches up to max_batch rows and inference in
+ * chunks of max_rows rows (both multiples of 128), up to max_groups shifts.
+ * Parameters start at zero: set them with haar_mlp_set_params. */
+HAAR_API haar_status_t haar_mlp_create(int max_batch, int max_rows, int max_groups, haar_mlp_t* out);
+HAAR_API haar_status_t haar_mlp_destroy(haar_mlp_t mlp);
+
+/* Copy the flat FP32 parameters in (any device- or host-accessible pointer,
+ * cudaMemcpyDefault) and reset the Adam state; or copy them out. */
+HAAR_API haar_status_t haar_mlp_set_params(haar_mlp_t mlp, const float* params, void* stream);
+HAAR_API haar_status_t haar_mlp_get_params(haar_mlp_t mlp, float* params, void* stream);
+
+/* out [B][512] float32 = network output for raw inputs [B][9]
+ * (position, normal, view direction); B a multiple of 128, <= max_batch. */
+HAAR_API haar_status_t haar_mlp_forward(haar_mlp_t mlp, const float* raw, int B, float* out, void* stream);
+
+/* Gradients of the mean squared error against target [B][512] into grads
+ * (flat, haar_mlp_param_count() floats; may be NULL) and the loss into
+ * loss[0] (device; may be NULL). */
+HAAR_API haar_status_t haar_mlp_grads(haar_mlp_t mlp, const float* raw, const float* target, int B, float* grads,
+                                      float* loss, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * mean squared error of batch (raw, target); loss[0] (device, may be NULL)
+ * receives the batch loss before the step. */
+HAAR_API haar_status_t haar_mlp_train_step(haar_mlp_t mlp, const float* raw, const float* target, int B, float lr,
+                                           float* loss, void* stream);
+
+/* Surrogate shading, fused: for every (s, v) the network evaluates the
+ * transport at the index set from (pos[v], nrm[v], normalize(cams[s] - pos[v]))
+ * and the last hidden layer's epilogue takes the double product with the
+ * shifted lighting, the output layer folded into the lighting per shift:
+ *   radiance[v][s][c] = sum_j (mu_j + sigma_j out_j) L(s, c, idx_j),
+ * L(s, c, k) = lighting[s * st_s + c * st_c + k * st_k] (float32, e.g. the
+ * output of haar_shift).  pos, nrm [V][3]; cams [S][3]; mu, sigma [512];
+ * idx [512] int32; C <= 4; radiance [V][S][C] float32. */
+HAAR_API haar_status_t haar_mlp_shade(haar_mlp_t mlp, int V, int S, const float* pos, const float* nrm,
+                                      const float* cams, const float* mu, const float* sigma, const int32_t* idx,
+                                      const float* lighting, int C, long long st_s, long long st_c, long long st_k,
+                                      float* radiance, void* stream);
+
+/* Copy and clear the surrogate's device status word (bit HAAR_ERR_TIMEOUT set
+ * when a bounded wait inside a tensor-core kernel gave up). Synchronous. */
+HAAR_API haar_status_t haar_mlp_status(haar_mlp_t mlp, int* out);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 HAAR_API const char* haar_last_error(void);
 

@@ -46,7 +46,9 @@ HAAR_T_BINCSR_F16_U32 = 3
 
 EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward",
            "haar_inverse", "shade_vertices", "shade_batch", "haar_view_bins",
-           "haar_last_error", "haar_version")
+           "haar_last_error", "haar_version", "haar_mlp_param_count", "haar_mlp_create",
+           "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params", "haar_mlp_forward",
+           "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status")
 
 
 class HaarShiftDesc(ctypes.Structure):
@@ -89,6 +91,21 @@ def lib() -> ctypes.CDLL:
     L.haar_view_bins.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp]
     for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward", "haar_inverse",
                  "shade_vertices", "shade_batch", "haar_view_bins"):
+        getattr(L, name).restype = st
+    ll = ctypes.c_longlong
+    L.haar_mlp_param_count.restype = ll
+    L.haar_mlp_param_count.argtypes = []
+    L.haar_mlp_create.argtypes = [i, i, i, ctypes.POINTER(vp)]
+    L.haar_mlp_destroy.argtypes = [vp]
+    L.haar_mlp_set_params.argtypes = [vp, vp, vp]
+    L.haar_mlp_get_params.argtypes = [vp, vp, vp]
+    L.haar_mlp_forward.argtypes = [vp, vp, i, vp, vp]
+    L.haar_mlp_grads.argtypes = [vp, vp, vp, i, vp, vp, vp]
+    L.haar_mlp_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, vp, vp]
+    L.haar_mlp_shade.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, i, ll, ll, ll, vp, vp]
+    L.haar_mlp_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    for name in ("haar_mlp_create", "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params",
+                 "haar_mlp_forward", "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status"):
         getattr(L, name).restype = st
     L.haar_last_error.restype = ctypes.c_char_p
     L.haar_last_error.argtypes = []
@@ -267,6 +284,82 @@ def haar_view_bins(pos, nrm, cams, bin_dirs, out=None, stream=None):
                                 _dev(cams, torch.float32, "cams"), _dev(bin_dirs, torch.float32, "bin_dirs"),
                                 _dev(out, torch.uint8, "bin_of"), _stream(stream)))
     return out
+
+
+class Surrogate:
+    """haar_mlp_t: the transport-surrogate MLP (training and fused shading)."""
+
+    N_IN, WIDTH, N_OUT, N_RAW = 320, 256, 512, 9
+
+    def __init__(self, max_batch=8192, max_rows=262144, max_groups=64):
+        h = ctypes.c_void_p()
+        _check(lib().haar_mlp_create(max_batch, max_rows, max_groups, ctypes.byref(h)))
+        self.handle = h.value
+        self.n_params = int(lib().haar_mlp_param_count())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().haar_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat, stream=None):
+        _check(lib().haar_mlp_set_params(self.handle, _dev(flat, None, "params"), _stream(stream)))
+
+    def get_params(self, stream=None):
+        import torch
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(lib().haar_mlp_get_params(self.handle, out.data_ptr(), _stream(stream)))
+        return out
+
+    def forward(self, raw, out=None, stream=None):
+        import torch
+        B = raw.shape[0]
+        if out is None:
+            out = torch.empty((B, self.N_OUT), dtype=torch.float32, device=raw.device)
+        _check(lib().haar_mlp_forward(self.handle, _dev(raw, torch.float32, "raw"), B,
+                                      _dev(out, torch.float32, "out"), _stream(stream)))
+        return out
+
+    def grads(self, raw, target, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=raw.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=raw.device)
+        _check(lib().haar_mlp_grads(self.handle, _dev(raw, torch.float32, "raw"), _dev(target, torch.float32, "target"),
+                                    raw.shape[0], g.data_ptr(), loss.data_ptr(), _stream(stream)))
+        return g, loss
+
+    def train_step(self, raw, target, lr, loss=None, stream=None):
+        import torch
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=raw.device)
+        _check(lib().haar_mlp_train_step(self.handle, _dev(raw, torch.float32, "raw"),
+                                         _dev(target, torch.float32, "target"), raw.shape[0], float(lr),
+                                         loss.data_ptr(), _stream(stream)))
+        return loss
+
+    def shade(self, pos, nrm, cams, mu, sigma, idx, lighting, C, strides, radiance=None, stream=None):
+        """radiance [V][S][C]; strides = (st_s, st_c, st_k) of the float32 lighting."""
+        import torch
+        V, S = pos.shape[0], cams.shape[0]
+        if radiance is None:
+            radiance = torch.empty((V, S, C), dtype=torch.float32, device=pos.device)
+        _check(lib().haar_mlp_shade(self.handle, V, S, _dev(pos, torch.float32, "pos"), _dev(nrm, torch.float32, "nrm"),
+                                    _dev(cams, torch.float32, "cams"), _dev(mu, torch.float32, "mu"),
+                                    _dev(sigma, torch.float32, "sigma"), _dev(idx, torch.int32, "idx"),
+                                    _dev(lighting, torch.float32, "lighting"), C, int(strides[0]), int(strides[1]),
+                                    int(strides[2]), _dev(radiance, torch.float32, "radiance"), _stream(stream)))
+        return radiance
+
+    def status(self) -> int:
+        v = ctypes.c_int(0)
+        _check(lib().haar_mlp_status(self.handle, ctypes.byref(v)))
+        return v.value
 
 
 def version() -> str:

@@ -23,6 +23,7 @@ haar_status_t set_error(haar_status_t st, const char* fmt, ...) {
 
 haar_status_t cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return HAAR_OK;
+  cudaGetLastError();  // a non-sticky failure must not surface again at the next launch
   return set_error(HAAR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 

@@ -16,130 +16,16 @@
 // Every mbarrier wait is bounded (by %globaltimer); on expiry the kernel
 // records HAAR_ERR_TIMEOUT in the status word, drains what it issued, frees
 // its tensor memory and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include "common.cuh"
+#include "tc.cuh"
 
 namespace hs {
 namespace tc {
 
-constexpr int BM = 128;            // vertices per tile (MMA M)
-constexpr int BK = 64;             // k per stage: 64 bf16 = one 128-byte swizzle row
-constexpr int STAGES = 3;
-constexpr int UMMA_K = 16;
 constexpr int THREADS = 192;       // 6 warps
-constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: false (and the status word / abort flag set) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status,
-                                          volatile int* abort_flag) {
-  for (int i = 0; i < 256; ++i)
-    if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > TIMEOUT_NS) {
-      atomicOr(status, 1 << HAAR_ERR_TIMEOUT);
-      *abort_flag = 1;
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// tcgen05 shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
-// 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);            // start address
-  d |= (uint64_t)1 << 16;                              // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                    // stride byte offset
-  d |= (uint64_t)1 << 46;                              // descriptor version
-  d |= (uint64_t)2 << 61;                              // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: bf16 x bf16 -> f32, K-major A and B.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4)                       // D format f32
-         | (1u << 7)                     // A format bf16
-         | (1u << 10)                    // B format bf16
-         | ((uint32_t)(N >> 3) << 17)    // N / 8
-         | ((uint32_t)(M >> 4) << 24);   // M / 16
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 struct __align__(8) Bars {
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
@@ -149,8 +35,8 @@ struct __align__(8) Bars {
 
 __global__ void __launch_bounds__(THREADS, 1)
 k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
-             const __grid_constant__ CUtensorMap mapBl, int V, int K, int N, float* __restrict__ R,
-             int* status) {
+             const __grid_constant__ CUtensorMap mapBl, int V, int K, int N, int STAGES,
+             float* __restrict__ R, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ Bars bars;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,9 +79,9 @@ k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapBl)) : "memory");
       int stage = 0;
       uint32_t phase = 0;
-      int issued[STAGES];
-      uint32_t issued_phase[STAGES];
-      for (int i = 0; i < STAGES; ++i) { issued[i] = 0; issued_phase[i] = 0; }
+      int issued[MAX_STAGES];
+      uint32_t issued_phase[MAX_STAGES];
+      for (int i = 0; i < MAX_STAGES; ++i) { issued[i] = 0; issued_phase[i] = 0; }
       bool ok = true;
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         for (int kb = 0; kb < kblocks; ++kb) {
@@ -295,33 +181,6 @@ k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
 
 }  // namespace tc
 
-static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (fn == nullptr) {
-    cudaDriverEntryPointQueryResult q;
-    void* p = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-static bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                      uint32_t box_outer) {
-  auto fn = get_encode();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {inner * 2};
-  cuuint32_t box[2] = {box_inner, box_outer};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 haar_status_t launch_shade_dense_bf16_tc(const __nv_bfloat16* T, int V, int K, const __nv_bfloat16* Lhi,
                                          const __nv_bfloat16* Llo, int ncols, float* R, int* status,
                                          cudaStream_t st) {
@@ -338,10 +197,13 @@ haar_status_t launch_shade_dense_bf16_tc(const __nv_bfloat16* T, int V, int K, c
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int n_tiles = (V + BM - 1) / BM;
   const int grid = n_tiles < sms ? n_tiles : sms;
-  const size_t smem = (size_t)STAGES * (BM * BK * 2 + 2 * (size_t)ncols * BK * 2) + 1024;
+  const size_t stage_bytes = BM * BK * 2 + 2 * (size_t)ncols * BK * 2;
+  int stages = (int)(SMEM_BUDGET / stage_bytes);
+  if (stages > MAX_STAGES) stages = MAX_STAGES;
+  const size_t smem = (size_t)stages * stage_bytes + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_dense_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_dense_bf16)");
-  k_dense_bf16<<<grid, THREADS, smem, st>>>(mA, mBh, mBl, V, K, ncols, R, status);
+  k_dense_bf16<<<grid, THREADS, smem, st>>>(mA, mBh, mBl, V, K, ncols, stages, R, status);
   return cuda_check(cudaGetLastError(), "k_dense_bf16 launch");
 }
 

@@ -1,0 +1,767 @@
+// Transport surrogate on sm_103a: a 4 x 256 GELU MLP that maps a vertex's
+// position, normal and view direction to its Haar transport coefficients at a
+// fixed index set, with BF16 tensor-core (tcgen05) forward and backward
+// GEMMs, FP32 accumulation, FP32 master weights and Adam, and an inference
+// path whose last hidden layer's epilogue performs the double product with
+// the shifted lighting directly (the output layer folded into the lighting).
+//
+// Encoding (9 inputs): x, then sin(w_f x), cos(w_f x) for w_f = pi 2^(f/2),
+// f = 0..15 (297 features, zero-padded to 320).  Flat parameter layout:
+// W1[256][320] b1[256] W2[256][256] b2 W3 b3 W4 b4 Wo[512][256] bo[512].
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "tc.cuh"
+
+namespace hs {
+namespace mlpk {
+
+constexpr int N_RAW = 9, N_FREQ = 16, N_IN = 320, WIDTH = 256, N_OUT = 512, N_LAYERS = 5;
+constexpr int THREADS = 192;
+
+__host__ __device__ constexpr int fan_in(int l) { return l == 0 ? N_IN : WIDTH; }
+__host__ __device__ constexpr int fan_out(int l) { return l == N_LAYERS - 1 ? N_OUT : WIDTH; }
+__host__ __device__ inline long long w_off(int l) {
+  long long o = 0;
+  for (int i = 0; i < l; ++i) o += (long long)fan_out(i) * fan_in(i) + fan_out(i);
+  return o;
+}
+__host__ __device__ inline long long b_off(int l) { return w_off(l) + (long long)fan_out(l) * fan_in(l); }
+constexpr long long N_PARAMS = (long long)WIDTH * N_IN + WIDTH + 3LL * (WIDTH * WIDTH + WIDTH) +
+                               (long long)N_OUT * WIDTH + N_OUT;
+
+enum Epi { EPI_F32 = 0, EPI_BIAS_GELU = 1, EPI_GELU_BWD = 2, EPI_SHADE = 3 };
+
+struct EpiArgs {
+  int M, N;
+  const float* bias;
+  float* out_f32;          // EPI_F32: out[m][n]; EPI_BIAS_GELU: pre-activation z (optional)
+  int ld_f32;
+  __nv_bfloat16* out_bf16; // EPI_BIAS_GELU: gelu(z); EPI_GELU_BWD: dz
+  int ld_bf16;
+  const float* zprev;      // EPI_GELU_BWD: pre-activation of the layer below
+  int ld_zprev;
+  const float* weff;       // EPI_SHADE: [groups][N][C]
+  const float* beff;       // EPI_SHADE: [groups][C]
+  int rows_per_group, groups, C, row0;
+  float* radiance;         // EPI_SHADE: R[v][s][c], row m + row0 = s * rows_per_group + v
+};
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+struct __align__(8) GBars {
+  uint64_t full[tc::MAX_STAGES];
+  uint64_t empty[tc::MAX_STAGES];
+  uint64_t tfull;
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+// C[M][N] = A[M][K] . B[N][K]^T, one 128 x BN tile per CTA; warp 0 TMA
+// producer, warp 1 MMA issuer, warps 2-5 epilogue.
+template <int EPI>
+__global__ void __launch_bounds__(THREADS, 1)
+k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K, int BN,
+       int STAGES, int tmem_cols, EpiArgs e, int* status) {
+  using namespace tc;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ GBars bars;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)BN * BK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const int kblocks = K / BK;
+  const int tm = blockIdx.x, tn = blockIdx.y;
+  volatile int* abort_flag = &bars.abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars.full[s]), 1);
+      mbar_init(smem_u32(&bars.empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bars.tfull), 1);
+    mbar_init(smem_u32(&bars.drain), 1);
+    bars.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars.tmem_base)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = bars.tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued[MAX_STAGES];
+      uint32_t issued_phase[MAX_STAGES];
+      for (int i = 0; i < MAX_STAGES; ++i) { issued[i] = 0; issued_phase[i] = 0; }
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        if (!mbar_wait(smem_u32(&bars.empty[stage]), phase ^ 1u, status, abort_flag)) break;
+        const uint32_t sa = base + stage * stage_bytes;
+        const uint32_t fb = smem_u32(&bars.full[stage]);
+        mbar_arrive_tx(fb, stage_bytes);
+        tma_load_2d(sa, &mapA, kb * BK, tm * BM, fb);
+        tma_load_2d(sa + a_bytes, &mapB, kb * BK, tn * BN, fb);
+        issued[stage] = 1;
+        issued_phase[stage] = phase;
+        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+      }
+      for (int i = 0; i < STAGES; ++i) {
+        if (!issued[i]) continue;
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try(smem_u32(&bars.full[i]), issued_phase[i]) && gtimer() - t0 < TIMEOUT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        if (!mbar_wait(smem_u32(&bars.full[stage]), phase, status, abort_flag)) { ok = false; break; }
+        fence_after();
+        const uint32_t sa = base + stage * stage_bytes;
+#pragma unroll
+        for (int k = 0; k < BK / UMMA_K; ++k)
+          mma_bf16(tmem, make_desc(sa + k * UMMA_K * 2), make_desc(sa + a_bytes + k * UMMA_K * 2), idesc,
+                   (kb | k) != 0 ? 1u : 0u);
+        mma_commit(smem_u32(&bars.empty[stage]));
+        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+      }
+      if (ok) mma_commit(smem_u32(&bars.tfull));
+      mma_commit(smem_u32(&bars.drain));
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try(smem_u32(&bars.drain), 0) && gtimer() - t0 < TIMEOUT_NS) {
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    const int m = tm * BM + quarter * 32 + lane;
+    if (mbar_wait(smem_u32(&bars.tfull), 0, status, abort_flag)) {
+      fence_after();
+      const uint32_t t_row = tmem + ((uint32_t)(quarter * 32) << 16);
+      float acc_c[4] = {0.f, 0.f, 0.f, 0.f};
+      int grp = 0;
+      if (EPI == EPI_SHADE) grp = (m + e.row0) / e.rows_per_group;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(t_row + (uint32_t)c0, v);
+        const int n0 = tn * BN + c0;
+        if (m >= e.M) continue;
+        if (EPI == EPI_F32) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = n0 + i;
+            if (n < e.N) e.out_f32[(long long)m * e.ld_f32 + n] = v[i] + (e.bias ? e.bias[n] : 0.0f);
+          }
+        } else if (EPI == EPI_BIAS_GELU) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = n0 + i;
+            if (n < e.N) {
+              const float z = v[i] + e.bias[n];
+              if (e.out_f32) e.out_f32[(long long)m * e.ld_f32 + n] = z;
+              e.out_bf16[(long long)m * e.ld_bf16 + n] = __float2bfloat16_rn(gelu(z));
+            }
+          }
+        } else if (EPI == EPI_GELU_BWD) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = n0 + i;
+            if (n < e.N)
+              e.out_bf16[(long long)m * e.ld_bf16 + n] =
+                  __float2bfloat16_rn(v[i] * gelu_grad(e.zprev[(long long)m * e.ld_zprev + n]));
+          }
+        } else {  // EPI_SHADE: fold gelu(z) against the per-group effective output weights
+          const float* W = e.weff + (long long)grp * e.N * e.C;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = n0 + i;
+            if (n < e.N) {
+              const float h = gelu(v[i] + e.bias[n]);
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (c < e.C) acc_c[c] = fmaf(h, __ldg(W + (long long)n * e.C + c), acc_c[c]);
+            }
+          }
+        }
+      }
+      if (EPI == EPI_SHADE && m < e.M) {
+        const int row = m + e.row0;
+        const int s = row / e.rows_per_group, vv = row - s * e.rows_per_group;
+        for (int c = 0; c < e.C; ++c)
+          e.radiance[((long long)vv * e.groups + s) * e.C + c] = acc_c[c] + e.beff[s * e.C + c];
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  }
+}
+
+// -------------------------------------------------------------- helper kernels
+
+__device__ __forceinline__ void encode_row(const float raw[N_RAW], __nv_bfloat16* out, int j0, int jstep) {
+  for (int j = j0; j < N_IN; j += jstep) {
+    float x = 0.0f;
+    if (j < N_RAW) {
+      x = raw[j];
+    } else if (j < N_RAW + 2 * N_FREQ * N_RAW) {
+      const int t = j - N_RAW;
+      const int f = t / (2 * N_RAW), r = t - f * 2 * N_RAW;
+      const float w = 3.14159265358979323846f * exp2f(0.5f * (float)f);
+      x = (r < N_RAW) ? sinf(w * raw[r]) : cosf(w * raw[r - N_RAW]);
+    }
+    out[j] = __float2bfloat16_rn(x);
+  }
+}
+
+// X[b][320] from raw inputs [b][9]
+__global__ void k_encode_raw(const float* __restrict__ raw, int B, __nv_bfloat16* __restrict__ X) {
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (b >= B) return;
+  float r[N_RAW];
+  for (int i = 0; i < N_RAW; ++i) r[i] = raw[(long long)b * N_RAW + i];
+  encode_row(r, X + (long long)b * N_IN, threadIdx.x & 31, 32);
+}
+
+// X[row][320] for rows row0.. of the (s, v) grid, row = s * V + v:
+// raw = (pos[v], nrm[v], normalize(cam[s] - pos[v]))
+__global__ void k_encode_scene(const float* __restrict__ pos, const float* __restrict__ nrm,
+                               const float* __restrict__ cams, int V, long long row0, int rows,
+                               __nv_bfloat16* __restrict__ X) {
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  const long long row = row0 + r;
+  const int s = (int)(row / V), v = (int)(row - (long long)s * V);
+  float raw[N_RAW];
+  for (int i = 0; i < 3; ++i) {
+    raw[i] = pos[3 * v + i];
+    raw[3 + i] = nrm[3 * v + i];
+  }
+  float wx = cams[3 * s] - raw[0], wy = cams[3 * s + 1] - raw[1], wz = cams[3 * s + 2] - raw[2];
+  const float inv = rsqrtf(wx * wx + wy * wy + wz * wz);
+  raw[6] = wx * inv; raw[7] = wy * inv; raw[8] = wz * inv;
+  encode_row(raw, X + (long long)r * N_IN, threadIdx.x & 31, 32);
+}
+
+// out[c][r] = in[r][c] (bf16), 32 x 32 tiles
+__global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int R, int C, __nv_bfloat16* __restrict__ out) {
+  __shared__ __nv_bfloat16 t[32][34];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < C) t[i][threadIdx.x] = in[(long long)r * C + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < C) out[(long long)c * R + r] = t[threadIdx.x][i];
+  }
+}
+
+// dOut = bf16(2 (out - y) / (B N)); loss += mean((out - y)^2)
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ y, long long n, float inv_n,
+                      __nv_bfloat16* __restrict__ dout, float* loss) {
+  float acc = 0.0f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = out[i] - y[i];
+    acc = fmaf(d, d, acc);
+    dout[i] = __float2bfloat16_rn(2.0f * d * inv_n);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    atomicAdd(loss, s * inv_n);
+  }
+}
+
+// db[n] = sum_b dz[b][n]
+__global__ void k_colsum(const __nv_bfloat16* __restrict__ dz, int B, int N, float* __restrict__ db) {
+  const int n = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int part = threadIdx.x >> 5, parts = blockDim.x >> 5;
+  float acc = 0.0f;
+  if (n < N)
+    for (int b = part; b < B; b += parts) acc += __bfloat162float(dz[(long long)b * N + n]);
+  __shared__ float red[8][32];
+  red[part][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (part == 0 && n < N) {
+    float s = 0.0f;
+    for (int p = 0; p < parts; ++p) s += red[p][threadIdx.x & 31];
+    db[n] = s;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// bf16 copies of every weight matrix ([out][in]) and of its transpose ([in][out])
+__global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long off = 0;
+  for (int l = 0; l < N_LAYERS; ++l) {
+    const long long sz = (long long)fan_out(l) * fan_in(l);
+    if (i < sz) {
+      const int o = (int)(i / fan_in(l)), in = (int)(i - (long long)o * fan_in(l));
+      const __nv_bfloat16 x = __float2bfloat16_rn(p[w_off(l) + i]);
+      wb[off + i] = x;
+      wt[off + (long long)in * fan_out(l) + o] = x;
+      return;
+    }
+    i -= sz;
+    off += sz;
+  }
+}
+
+// Output layer folded into the lighting, per group s:
+//   Weff[s][i][c] = sum_j Wo[j][i] sigma_j L(s, c, idx_j)
+//   beff[s][c]    = sum_j (mu_j + sigma_j bo_j) L(s, c, idx_j)
+__global__ void k_fold(const float* __restrict__ p, const float* __restrict__ mu, const float* __restrict__ sigma,
+                       const int* __restrict__ idx, const float* __restrict__ L, long long st_s, long long st_c,
+                       long long st_k, int S, int C, float* __restrict__ weff, float* __restrict__ beff) {
+  const int s = blockIdx.x;
+  const float* Wo = p + w_off(N_LAYERS - 1);
+  const float* bo = p + b_off(N_LAYERS - 1);
+  __shared__ float sl[N_OUT][4];
+  for (int j = threadIdx.x; j < N_OUT; j += blockDim.x)
+    for (int c = 0; c < 4; ++c)
+      sl[j][c] = (c < C) ? sigma[j] * L[s * st_s + c * st_c + (long long)idx[j] * st_k] : 0.0f;
+  __syncthreads();
+  for (int t = threadIdx.x; t < WIDTH * C; t += blockDim.x) {
+    const int i = t / C, c = t - i * C;
+    float acc = 0.0f;
+    for (int j = 0; j < N_OUT; ++j) acc = fmaf(Wo[(long long)j * WIDTH + i], sl[j][c], acc);
+    weff[((long long)s * WIDTH + i) * C + c] = acc;
+  }
+  if (threadIdx.x < C) {
+    const int c = threadIdx.x;
+    float acc = 0.0f;
+    for (int j = 0; j < N_OUT; ++j) {
+      const float lj = L[s * st_s + c * st_c + (long long)idx[j] * st_k];
+      acc = fmaf(mu[j] + sigma[j] * bo[j], lj, acc);
+    }
+    beff[s * C + c] = acc;
+  }
+}
+
+}  // namespace mlpk
+}  // namespace hs
+
+using namespace hs;
+using namespace hs::mlpk;
+
+struct haar_mlp_s {
+  int max_batch, max_rows, max_groups;
+  float* p;           // master parameters (flat, FP32)
+  float* g;           // gradients (flat)
+  float* m;           // Adam first moments
+  float* v;           // Adam second moments
+  __nv_bfloat16* wb;  // bf16 weights, [out][in] per layer
+  __nv_bfloat16* wt;  // bf16 transposed weights, [in][out] per layer
+  int adam_t;
+  // training buffers (max_batch rows)
+  __nv_bfloat16* X;   // [B][320]
+  __nv_bfloat16* h[4];// [B][256]
+  float* z[4];        // [B][256]
+  float* out;         // [B][512]
+  __nv_bfloat16* dout;// [B][512]
+  __nv_bfloat16* dz;  // [B][256]
+  __nv_bfloat16* dz2; // [B][256]
+  __nv_bfloat16* tA;  // transpose scratch [512][B]
+  __nv_bfloat16* tB;  // transpose scratch [320][B]
+  float* loss;        // [1]
+  // inference buffers (max_rows rows)
+  __nv_bfloat16* iX;  // [rows][320]
+  __nv_bfloat16* ih0; // [rows][256]
+  __nv_bfloat16* ih1; // [rows][256]
+  float* weff;        // [groups][256][4]
+  float* beff;        // [groups][4]
+  int* status;
+};
+
+namespace hs {
+namespace mlpk {
+
+static size_t w_total() {
+  size_t t = 0;
+  for (int l = 0; l < N_LAYERS; ++l) t += (size_t)fan_out(l) * fan_in(l);
+  return t;
+}
+static size_t wb_off(int l) {
+  size_t t = 0;
+  for (int i = 0; i < l; ++i) t += (size_t)fan_out(i) * fan_in(i);
+  return t;
+}
+
+template <int EPI>
+static haar_status_t gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int K, const EpiArgs& e,
+                          int* status, cudaStream_t st) {
+  using namespace tc;
+  if (K % BK != 0) return set_error(HAAR_ERR_INVALID_ARG, "mlp gemm: K = %d is not a multiple of 64", K);
+  const int ntiles = (N + 255) / 256;
+  int BN = (N + ntiles - 1) / ntiles;
+  BN = (BN + 15) / 16 * 16;
+  if (EPI == EPI_SHADE && ntiles != 1) return set_error(HAAR_ERR_UNSUPPORTED, "mlp gemm: shade epilogue needs N <= 256");
+  CUtensorMap mA, mB;
+  if (!encode_2d(&mA, A, (uint64_t)K, (uint64_t)M, BK, BM) || !encode_2d(&mB, B, (uint64_t)K, (uint64_t)N, BK, (uint32_t)BN))
+    return set_error(HAAR_ERR_CUDA, "mlp gemm: cuTensorMapEncodeTiled failed");
+  const size_t stage = (size_t)BM * BK * 2 + (size_t)BN * BK * 2;
+  int stages = (int)(SMEM_BUDGET / stage);
+  if (stages > MAX_STAGES) stages = MAX_STAGES;
+  const size_t smem = (size_t)stages * stage + 1024;
+  int tcols = 32;
+  while (tcols < BN) tcols <<= 1;
+  cudaError_t err = cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return cuda_check(err, "cudaFuncSetAttribute(k_gemm)");
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  k_gemm<EPI><<<grid, THREADS, smem, st>>>(mA, mB, K, BN, stages, tcols, e, status);
+  return cuda_check(cudaGetLastError(), "k_gemm launch");
+}
+
+static EpiArgs epi(int M, int N) {
+  EpiArgs e;
+  memset(&e, 0, sizeof(e));
+  e.M = M;
+  e.N = N;
+  return e;
+}
+
+static haar_status_t transpose(const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out, cudaStream_t st) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+  k_transpose<<<grid, block, 0, st>>>(in, R, C, out);
+  return cuda_check(cudaGetLastError(), "k_transpose launch");
+}
+
+#define HS_TRY(x)                   \
+  do {                              \
+    haar_status_t _r = (x);         \
+    if (_r != HAAR_OK) return _r;   \
+  } while (0)
+
+// forward over B rows of encoded inputs in M->X; keeps z and h for backward
+static haar_status_t forward(haar_mlp_s* M, int B, cudaStream_t st) {
+  const __nv_bfloat16* in = M->X;
+  for (int l = 0; l < 4; ++l) {
+    EpiArgs e = epi(B, WIDTH);
+    e.bias = M->p + b_off(l);
+    e.out_f32 = M->z[l];
+    e.ld_f32 = WIDTH;
+    e.out_bf16 = M->h[l];
+    e.ld_bf16 = WIDTH;
+    HS_TRY(gemm<EPI_BIAS_GELU>(in, B, M->wb + wb_off(l), WIDTH, fan_in(l), e, M->status, st));
+    in = M->h[l];
+  }
+  EpiArgs e = epi(B, N_OUT);
+  e.bias = M->p + b_off(4);
+  e.out_f32 = M->out;
+  e.ld_f32 = N_OUT;
+  return gemm<EPI_F32>(M->h[3], B, M->wb + wb_off(4), N_OUT, WIDTH, e, M->status, st);
+}
+
+static haar_status_t backward(haar_mlp_s* M, int B, const float* target, cudaStream_t st) {
+  const long long n = (long long)B * N_OUT;
+  k_mse<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(M->out, target, n, 1.0f / (float)n,
+                                                                                  M->dout, M->loss);
+  HS_TRY(cuda_check(cudaGetLastError(), "k_mse launch"));
+  // output layer
+  HS_TRY(transpose(M->dout, B, N_OUT, M->tA, st));
+  HS_TRY(transpose(M->h[3], B, WIDTH, M->tB, st));
+  {
+    EpiArgs e = epi(N_OUT, WIDTH);
+    e.out_f32 = M->g + w_off(4);
+    e.ld_f32 = WIDTH;
+    HS_TRY(gemm<EPI_F32>(M->tA, N_OUT, M->tB, WIDTH, B, e, M->status, st));
+  }
+  k_colsum<<<(N_OUT + 31) / 32, 256, 0, st>>>(M->dout, B, N_OUT, M->g + b_off(4));
+  HS_TRY(cuda_check(cudaGetLastError(), "k_colsum launch"));
+  {
+    EpiArgs e = epi(B, WIDTH);
+    e.out_bf16 = M->dz;
+    e.ld_bf16 = WIDTH;
+    e.zprev = M->z[3];
+    e.ld_zprev = WIDTH;
+    HS_TRY(gemm<EPI_GELU_BWD>(M->dout, B, M->wt + wb_off(4), WIDTH, N_OUT, e, M->status, st));
+  }
+  __nv_bfloat16* dz = M->dz;
+  __nv_bfloat16* dz_next = M->dz2;
+  for (int l = 3; l >= 0; --l) {
+    const int fin = fan_in(l);
+    const __nv_bfloat16* hin = (l == 0) ? M->X : M->h[l - 1];
+    HS_TRY(transpose(dz, B, WIDTH, M->tA, st));
+    HS_TRY(transpose(hin, B, fin, M->tB, st));
+    EpiArgs e = epi(WIDTH, fin);
+    e.out_f32 = M->g + w_off(l);
+    e.ld_f32 = fin;
+    HS_TRY(gemm<EPI_F32>(M->tA, WIDTH, M->tB, fin, B, e, M->status, st));
+    k_colsum<<<(WIDTH + 31) / 32, 256, 0, st>>>(dz, B, WIDTH, M->g + b_off(l));
+    HS_TRY(cuda_check(cudaGetLastError(), "k_colsum launch"));
+    if (l > 0) {
+      EpiArgs d = epi(B, WIDTH);
+      d.out_bf16 = dz_next;
+      d.ld_bf16 = WIDTH;
+      d.zprev = M->z[l - 1];
+      d.ld_zprev = WIDTH;
+      HS_TRY(gemm<EPI_GELU_BWD>(dz, B, M->wt + wb_off(l), WIDTH, WIDTH, d, M->status, st));
+      __nv_bfloat16* t = dz; dz = dz_next; dz_next = t;
+    }
+  }
+  return HAAR_OK;
+}
+
+static haar_status_t pack(haar_mlp_s* M, cudaStream_t st) {
+  const long long n = (long long)w_total();
+  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M->p, M->wb, M->wt);
+  return cuda_check(cudaGetLastError(), "k_pack launch");
+}
+
+static haar_status_t encode_raw(haar_mlp_s* M, const float* raw, int B, cudaStream_t st) {
+  k_encode_raw<<<(B + 7) / 8, 256, 0, st>>>(raw, B, M->X);
+  return cuda_check(cudaGetLastError(), "k_encode_raw launch");
+}
+
+}  // namespace mlpk
+}  // namespace hs
+
+#define HS_ENTRY(name)                                              \
+  if (injected(name)) return set_error(HAAR_ERR_INJECTED, "%s: injected fault", name)
+
+static void mlp_free(haar_mlp_s* M) {
+  if (!M) return;
+  void* ptrs[] = {M->p, M->g, M->m, M->v, M->wb, M->wt, M->X, M->h[0], M->h[1], M->h[2], M->h[3], M->z[0],
+                  M->z[1], M->z[2], M->z[3], M->out, M->dout, M->dz, M->dz2, M->tA, M->tB, M->loss, M->iX,
+                  M->ih0, M->ih1, M->weff, M->beff, M->status};
+  for (void* q : ptrs) cudaFree(q);
+  delete M;
+}
+
+extern "C" {
+
+long long haar_mlp_param_count(void) { return N_PARAMS; }
+
+haar_status_t haar_mlp_create(int max_batch, int max_rows, int max_groups, haar_mlp_t* out) {
+  HS_ENTRY("haar_mlp_create");
+  if (out == nullptr) return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_create: null output");
+  *out = nullptr;
+  if (max_batch < 128 || max_batch % 128 != 0 || max_batch > (1 << 22))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_create: max_batch %d must be a multiple of 128", max_batch);
+  if (max_rows < 128 || max_rows % 128 != 0 || max_groups < 1 || max_groups > 65535)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_create: max_rows %d (multiple of 128), max_groups %d", max_rows,
+                     max_groups);
+  haar_mlp_s* M = new (std::nothrow) haar_mlp_s();
+  if (!M) return set_error(HAAR_ERR_NOMEM, "haar_mlp_create: host allocation failed");
+  memset(M, 0, sizeof(*M));
+  M->max_batch = max_batch;
+  M->max_rows = max_rows;
+  M->max_groups = max_groups;
+  const size_t B = max_batch, R = max_rows, P = N_PARAMS, WT = w_total();
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) \
+  if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes))
+  ALLOC(M->p, P * 4);
+  ALLOC(M->g, P * 4);
+  ALLOC(M->m, P * 4);
+  ALLOC(M->v, P * 4);
+  ALLOC(M->wb, WT * 2);
+  ALLOC(M->wt, WT * 2);
+  ALLOC(M->X, B * N_IN * 2);
+  for (int l = 0; l < 4; ++l) {
+    ALLOC(M->h[l], B * WIDTH * 2);
+    ALLOC(M->z[l], B * WIDTH * 4);
+  }
+  ALLOC(M->out, B * N_OUT * 4);
+  ALLOC(M->dout, B * N_OUT * 2);
+  ALLOC(M->dz, B * WIDTH * 2);
+  ALLOC(M->dz2, B * WIDTH * 2);
+  ALLOC(M->tA, B * N_OUT * 2);
+  ALLOC(M->tB, B * N_IN * 2);
+  ALLOC(M->loss, 4);
+  ALLOC(M->iX, R * N_IN * 2);
+  ALLOC(M->ih0, R * WIDTH * 2);
+  ALLOC(M->ih1, R * WIDTH * 2);
+  ALLOC(M->weff, (size_t)max_groups * WIDTH * 4 * 4);
+  ALLOC(M->beff, (size_t)max_groups * 4 * 4);
+  ALLOC(M->status, 16);
+#undef ALLOC
+  if (e != cudaSuccess) {
+    mlp_free(M);
+    return set_error(HAAR_ERR_NOMEM, "haar_mlp_create: allocation failed: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemset(M->p, 0, P * 4);
+  if (e == cudaSuccess) e = cudaMemset(M->m, 0, P * 4);
+  if (e == cudaSuccess) e = cudaMemset(M->v, 0, P * 4);
+  if (e == cudaSuccess) e = cudaMemset(M->status, 0, 16);
+  if (e == cudaSuccess) e = cudaMemset(M->loss, 0, 4);
+  if (e != cudaSuccess) {
+    mlp_free(M);
+    return cuda_check(e, "haar_mlp_create: cudaMemset");
+  }
+  *out = M;
+  return HAAR_OK;
+}
+
+haar_status_t haar_mlp_destroy(haar_mlp_t M) {
+  HS_ENTRY("haar_mlp_destroy");
+  if (!M) return HAAR_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  mlp_free(M);
+  return cuda_check(e, "haar_mlp_destroy: synchronise");
+}
+
+haar_status_t haar_mlp_set_params(haar_mlp_t M, const float* params, void* stream) {
+  HS_ENTRY("haar_mlp_set_params");
+  if (!M || !params) return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_set_params: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(M->p, params, N_PARAMS * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(M->m, 0, N_PARAMS * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(M->v, 0, N_PARAMS * 4, st);
+  if (e != cudaSuccess) return cuda_check(e, "haar_mlp_set_params");
+  M->adam_t = 0;
+  return pack(M, st);
+}
+
+haar_status_t haar_mlp_get_params(haar_mlp_t M, float* params, void* stream) {
+  HS_ENTRY("haar_mlp_get_params");
+  if (!M || !params) return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_get_params: null argument");
+  return cuda_check(cudaMemcpyAsync(params, M->p, N_PARAMS * 4, cudaMemcpyDefault, (cudaStream_t)stream),
+                    "haar_mlp_get_params");
+}
+
+static haar_status_t check_batch(haar_mlp_t M, int B, const char* who) {
+  if (!M) return set_error(HAAR_ERR_INVALID_ARG, "%s: null surrogate", who);
+  if (B < 128 || B % 128 != 0 || B > M->max_batch)
+    return set_error(HAAR_ERR_INVALID_ARG, "%s: batch %d must be a multiple of 128 in [128, %d]", who, B, M->max_batch);
+  return HAAR_OK;
+}
+
+haar_status_t haar_mlp_forward(haar_mlp_t M, const float* raw, int B, float* out, void* stream) {
+  HS_ENTRY("haar_mlp_forward");
+  haar_status_t r = check_batch(M, B, "haar_mlp_forward");
+  if (r != HAAR_OK) return r;
+  if (!raw || !out) return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_forward: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  HS_TRY(encode_raw(M, raw, B, st));
+  HS_TRY(forward(M, B, st));
+  return cuda_check(cudaMemcpyAsync(out, M->out, (size_t)B * N_OUT * 4, cudaMemcpyDeviceToDevice, st),
+                    "haar_mlp_forward: copy");
+}
+
+haar_status_t haar_mlp_grads(haar_mlp_t M, const float* raw, const float* target, int B, float* grads, float* loss,
+                             void* stream) {
+  HS_ENTRY("haar_mlp_grads");
+  haar_status_t r = check_batch(M, B, "haar_mlp_grads");
+  if (r != HAAR_OK) return r;
+  if (!raw || !target) return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_grads: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  HS_TRY(cuda_check(cudaMemsetAsync(M->loss, 0, 4, st), "haar_mlp_grads: memset"));
+  HS_TRY(encode_raw(M, raw, B, st));
+  HS_TRY(forward(M, B, st));
+  HS_TRY(backward(M, B, target, st));
+  if (grads)
+    HS_TRY(cuda_check(cudaMemcpyAsync(grads, M->g, N_PARAMS * 4, cudaMemcpyDeviceToDevice, st), "haar_mlp_grads: copy"));
+  if (loss) HS_TRY(cuda_check(cudaMemcpyAsync(loss, M->loss, 4, cudaMemcpyDeviceToDevice, st), "haar_mlp_grads: loss"));
+  return HAAR_OK;
+}
+
+haar_status_t haar_mlp_train_step(haar_mlp_t M, const float* raw, const float* target, int B, float lr, float* loss,
+                                  void* stream) {
+  HS_ENTRY("haar_mlp_train_step");
+  haar_status_t r = check_batch(M, B, "haar_mlp_train_step");
+  if (r != HAAR_OK) return r;
+  if (!raw || !target) return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_train_step: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  HS_TRY(cuda_check(cudaMemsetAsync(M->loss, 0, 4, st), "haar_mlp_train_step: memset"));
+  HS_TRY(encode_raw(M, raw, B, st));
+  HS_TRY(forward(M, B, st));
+  HS_TRY(backward(M, B, target, st));
+  M->adam_t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - powf(b1, (float)M->adam_t), c2 = 1.0f - powf(b2, (float)M->adam_t);
+  k_adam<<<1024, 256, 0, st>>>(M->p, M->g, M->m, M->v, N_PARAMS, lr, b1, b2, 1e-8f, c1, c2);
+  HS_TRY(cuda_check(cudaGetLastError(), "k_adam launch"));
+  HS_TRY(pack(M, st));
+  if (loss) HS_TRY(cuda_check(cudaMemcpyAsync(loss, M->loss, 4, cudaMemcpyDeviceToDevice, st), "haar_mlp_train_step: loss"));
+  return HAAR_OK;
+}
+
+haar_status_t haar_mlp_shade(haar_mlp_t M, int V, int S, const float* pos, const float* nrm, const float* cams,
+                             const float* mu, const float* sigma, const int32_t* idx, const float* lighting, int C,
+                             long long st_s, long long st_c, long long st_k, float* radiance, void* stream) {
+  HS_ENTRY("haar_mlp_shade");
+  if (!M || !pos || !nrm || !cams || !mu || !sigma || !idx || !lighting || !radiance)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_shade: null argument");
+  if (V < 1 || S < 1 || S > M->max_groups || C < 1 || C > 4)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_shade: V=%d S=%d (max %d) C=%d (1..4)", V, S, M->max_groups, C);
+  cudaStream_t st = (cudaStream_t)stream;
+  k_fold<<<S, 256, 0, st>>>(M->p, mu, sigma, idx, lighting, st_s, st_c, st_k, S, C, M->weff, M->beff);
+  HS_TRY(cuda_check(cudaGetLastError(), "k_fold launch"));
+  const long long rows = (long long)V * S;
+  for (long long r0 = 0; r0 < rows; r0 += M->max_rows) {
+    const int n = (int)((rows - r0) < M->max_rows ? (rows - r0) : M->max_rows);
+    k_encode_scene<<<(n + 7) / 8, 256, 0, st>>>(pos, nrm, cams, V, r0, n, M->iX);
+    HS_TRY(cuda_check(cudaGetLastError(), "k_encode_scene launch"));
+    const __nv_bfloat16* in = M->iX;
+    __nv_bfloat16* bufs[2] = {M->ih0, M->ih1};
+    for (int l = 0; l < 3; ++l) {
+      EpiArgs e = epi(n, WIDTH);
+      e.bias = M->p + b_off(l);
+      e.out_bf16 = bufs[l & 1];
+      e.ld_bf16 = WIDTH;
+      HS_TRY(gemm<EPI_BIAS_GELU>(in, n, M->wb + wb_off(l), WIDTH, fan_in(l), e, M->status, st));
+      in = bufs[l & 1];
+    }
+    EpiArgs e = epi(n, WIDTH);
+    e.bias = M->p + b_off(3);
+    e.weff = M->weff;
+    e.beff = M->beff;
+    e.rows_per_group = V;
+    e.groups = S;
+    e.C = C;
+    e.row0 = (int)r0;
+    e.radiance = radiance;
+    HS_TRY(gemm<EPI_SHADE>(in, n, M->wb + wb_off(3), WIDTH, WIDTH, e, M->status, st));
+  }
+  return HAAR_OK;
+}
+
+haar_status_t haar_mlp_status(haar_mlp_t M, int* out) {
+  HS_ENTRY("haar_mlp_status");
+  if (!M || !out) return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_status: null argument");
+  cudaError_t e = cudaMemcpy(out, M->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(M->status, 0, sizeof(int));
+  return cuda_check(e, "haar_mlp_status");
+}
+
+}  // extern "C"
