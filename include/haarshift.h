@@ -126,6 +126,31 @@ HAAR_API haar_status_t haar_shift_plan_destroy(haar_shift_plan_t plan);
 HAAR_API haar_status_t haar_shift(haar_shift_plan_t plan, const float* coeffs_in, const double* params,
                          int S, void* coeffs_out, void* stream);
 
+/* The phase shift of haar_shift without a plan and without allocating.
+ * (The paper has no counterpart; this is a calling convenience.)  For callers
+ * that cannot allocate device memory at all: plug-ins inside a host renderer
+ * or engine whose device memory belongs to the host's own allocator, and
+ * real-time frame loops that may not call cudaMalloc/cudaFree, which
+ * synchronise the device.  It computes exactly what haar_shift computes for
+ * the same descriptor (desc->max_shifts is ignored; S is this call's count)
+ * and calls no cudaMalloc, cudaFree or allocating library routine: its
+ * scratch is one fixed array of 2 Mi floats (8 MiB) in the library's device
+ * memory, which every GPU that loads the library holds until the process
+ * exits.  A call needs C*H*W + 2*(H+W) + S*(20 + C*T + 1) floats, T = H*W/4096
+ * tiles for H >= 64 (1 or 2 below), each part rounded up to 64; larger calls
+ * are rejected with HAAR_ERR_INVALID_ARG and a message giving both sizes
+ * (RGB 256x512 fits with up to several thousand shifts; RGB 1024x2048 does
+ * not fit).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array
+ * and it keeps the previous call's contents (the call clears the tile
+ * counters it needs at zero itself): calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results; order them.
+ * coeffs_in, params, coeffs_out: as for haar_shift (device memory). */
+HAAR_API haar_status_t haar_shift_noalloc(const haar_shift_desc_t* desc, const float* coeffs_in,
+                                          const double* params, int S, void* coeffs_out, void* stream);
+
 /* Forward orthonormal Haar transform of `batch` H x W float32 maps
  * ([batch][H][W] row-major) into [batch][N] canonical coefficients; `scale`
  * multiplies every output (1.0 for the plain transform). */

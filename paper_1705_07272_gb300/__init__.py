@@ -48,7 +48,8 @@ EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_for
            "haar_inverse", "shade_vertices", "shade_batch", "haar_view_bins",
            "haar_last_error", "haar_version", "haar_mlp_param_count", "haar_mlp_create",
            "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params", "haar_mlp_forward",
-           "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status")
+           "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status",
+           "haar_shift_noalloc")
 
 
 class HaarShiftDesc(ctypes.Structure):
@@ -84,12 +85,13 @@ def lib() -> ctypes.CDLL:
     L.haar_shift_plan.argtypes = [ctypes.POINTER(HaarShiftDesc), ctypes.POINTER(vp)]
     L.haar_shift_plan_destroy.argtypes = [vp]
     L.haar_shift.argtypes = [vp, vp, vp, i, vp, vp]
+    L.haar_shift_noalloc.argtypes = [ctypes.POINTER(HaarShiftDesc), vp, vp, i, vp, vp]
     L.haar_forward.argtypes = [i, i, i, vp, vp, ctypes.c_float, vp]
     L.haar_inverse.argtypes = [i, i, i, vp, vp, vp]
     L.shade_vertices.argtypes = [vp, ctypes.POINTER(HaarTransportDesc), vp, i, vp, vp]
     L.shade_batch.argtypes = [vp, vp, vp, i, ctypes.POINTER(HaarTransportDesc), vp, vp]
     L.haar_view_bins.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp]
-    for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward", "haar_inverse",
+    for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_shift_noalloc", "haar_forward", "haar_inverse",
                  "shade_vertices", "shade_batch", "haar_view_bins"):
         getattr(L, name).restype = st
     ll = ctypes.c_longlong

@@ -1,0 +1,105 @@
+// haar_shift_noalloc: the phase shift without a plan and without any
+// device allocation.
+//
+// Some callers cannot allocate device memory: plug-ins inside a host renderer
+// or engine whose device memory is owned by the host's own allocator, and
+// real-time frame loops that may not call cudaMalloc/cudaFree (they
+// synchronise the device and can stall a frame).  This entry point runs the
+// same set-up and shift kernels as haar_shift, but its scratch (pixel map,
+// sin/cos tables, shift records, tile means, tile counters) lives in one
+// file-scope __device__ array of fixed size, so the caller passes only inputs
+// and outputs.
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace hs {
+
+// 2 Mi floats = 8 MiB of scratch, held by every GPU that loads the library
+// until the process exits.
+constexpr size_t kNoAllocFloats = size_t(2) << 20;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+constexpr int kMaxDevices = 64;
+static float* g_noalloc_ptr[kMaxDevices];
+static std::mutex g_noalloc_mu;
+
+static size_t round64(size_t x) { return (x + 63) & ~size_t(63); }
+
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const float* cin, const double* params,
+                                            int S, void* out, void* stream) {
+  if (injected("haar_shift_noalloc")) return set_error(HAAR_ERR_INJECTED, "haar_shift_noalloc: injected fault");
+  if (d == nullptr || cin == nullptr || params == nullptr || out == nullptr)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: null argument");
+  const int H = d->height, W = d->width, C = d->channels;
+  if (H < 2 || H > 4096 || (H & (H - 1)) != 0 || (W != H && W != 2 * H))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: unsupported map %dx%d", H, W);
+  if (C < 1 || C > 64) return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: channels %d not in [1, 64]", C);
+  if (d->kind < HAAR_SHIFT_TRANSLATE || d->kind > HAAR_SHIFT_ROTATE_EULER ||
+      (d->boundary != HAAR_BOUNDARY_SPHERE && d->boundary != HAAR_BOUNDARY_TORUS) ||
+      d->out_type < HAAR_OUT_F32 || d->out_type > HAAR_OUT_F16 || d->out_layout < HAAR_LAYOUT_SCK ||
+      d->out_layout > HAAR_LAYOUT_KSC)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: unknown kind, boundary, out_type or out_layout");
+  const long long N = (long long)H * W;
+  if (d->out_coeffs < 0 || d->out_coeffs > N)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: out_coeffs %d not in [0, %lld]", d->out_coeffs, N);
+  if (S < 1 || S > 65535) return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: S = %d not in [1, 65535]", S);
+  const size_t elem = d->out_type == HAAR_OUT_F32 ? 4 : 2;
+  if (((uintptr_t)cin % 4) || ((uintptr_t)params % 8) || ((uintptr_t)out % elem))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: misaligned pointer");
+
+  // scratch layout (floats, each region 256-byte aligned)
+  const Geometry g = make_geometry(H, W, C, d->boundary);
+  const size_t n_pix = round64((size_t)C * N);
+  const size_t n_trig = round64(2 * (size_t)(H + W));
+  const size_t n_prm = round64((size_t)S * sizeof(ShiftParam) / sizeof(float));
+  const size_t n_means = round64((size_t)S * C * g.n_tiles);
+  const size_t n_cnt = round64((size_t)S);
+  const size_t need = n_pix + n_trig + n_prm + n_means + n_cnt;
+  if (need > kNoAllocFloats)
+    return set_error(HAAR_ERR_INVALID_ARG,
+                     "haar_shift_noalloc: needs %zu scratch floats (C*H*W + tables for S = %d shifts), the fixed "
+                     "maximum is %zu", need, S, kNoAllocFloats);
+
+  // once per device: the device address of the scratch array
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_check(e, "haar_shift_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return set_error(HAAR_ERR_UNSUPPORTED, "haar_shift_noalloc: device %d", dev);
+  float* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_check(e, "haar_shift_noalloc: cudaGetSymbolAddress");
+      g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+
+  haar_shift_plan_s p;
+  memset(&p, 0, sizeof(p));
+  p.desc = *d;
+  p.desc.max_shifts = S;
+  p.geo = g;
+  p.K = d->out_coeffs ? d->out_coeffs : (int)N;
+  p.device = dev;
+  p.pix = base;
+  p.trig = base + n_pix;
+  p.prm = reinterpret_cast<ShiftParam*>(base + n_pix + n_trig);
+  p.means = base + n_pix + n_trig + n_prm;
+  p.counters = reinterpret_cast<unsigned*>(base + n_pix + n_trig + n_prm + n_means);
+  cudaStream_t st = (cudaStream_t)stream;
+  haar_status_t r = HAAR_OK;
+  if (d->kind != HAAR_SHIFT_TRANSLATE) r = launch_trig(&p, st);     // tables of this call's map
+  if (r == HAAR_OK) r = launch_setup(&p, cin, params, S, st);        // also zeroes the tile counters
+  if (r == HAAR_OK) r = launch_shift(&p, cin, S, out, st);
+  return r;
+}
