@@ -30,7 +30,8 @@ if ROOT not in sys.path:
 METRIC = "M vertex-rotations/s and % of HBM/tensor roofline; BF16+surrogate vs FP32 plain"
 UNIT = "M vertex-rotations/s"
 WORKLOAD = ("RGB 128x256 lat-long lighting (32768 Haar coefficients per channel), 16 fractional "
-            "shifts per frame, 50000 torus vertices (8 occluders), top-256 CSR FP32 transport")
+            "shifts per frame, 50000 torus vertices (8 occluders), top-256 CSR FP32 transport "
+            "(repacked as 8-vertex group CSR)")
 FLUSH_BYTES = 256 << 20
 
 
@@ -41,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements of the other configs")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated rows to run alone (no c1 frame), for profiling one kernel")
     ap.add_argument("--cpu-sample", type=int, default=2000, help="vertices in the oracle's timed sample")
     return ap.parse_args()
 
@@ -107,15 +111,42 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- GPU workload
 
+def shard_vertices(cid: int, rank: int, V: int):
+    """Vertex shard of a rank: rank 0 uses the workload's own vertices, rank r
+    an independent draw of the same surface (weak scaling, no overlap)."""
+    import synth
+    sc = synth.scene(cid, V=V)
+    if rank == 0:
+        return sc["pos"], sc["nrm"]
+    rg = synth.rng_for(cid, 100 + rank)
+    if synth.WORKLOADS[cid].surface == "sphere":
+        return synth.sphere_vertices(rg, V)
+    return synth.torus_vertices(rg, V)
+
+
+def max_over_ranks(x: float, dev) -> float:
+    """The largest value over all ranks (the slowest rank's time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: int, ms: float, world: int) -> float:
+    """Units of all ranks per second, in millions."""
+    return units_per_rank * world / (ms * 1e-3) / 1e6
+
+
 def prepare_c1(hs, dev, rank: int):
     """Device-resident c1 frame: lighting coefficients, shifts, CSR transport."""
     import numpy as np
     import torch
     import synth
     sc = synth.scene(1)
-    if rank:
-        rg = synth.rng_for(1, 100 + rank)
-        sc["pos"], sc["nrm"] = synth.torus_vertices(rg, sc["V"])
+    sc["pos"], sc["nrm"] = shard_vertices(1, rank, sc["V"])
     H, W, C, S, V = sc["H"], sc["W"], sc["C"], sc["S"], sc["V"]
     light = torch.tensor(sc["light"], dtype=torch.float32, device=dev)
     L = hs.haar_forward(light).contiguous()                                    # [3, 32768]
@@ -126,7 +157,7 @@ def prepare_c1(hs, dev, rank: int):
     for v0 in range(0, V, chunk):
         v1 = min(V, v0 + chunk)
         w = synth.transport_weights(sc["pos"][v0:v1], sc["nrm"][v0:v1], sc["occ_c"], sc["occ_r"], H, W,
-                                    device=dev, dtype=torch.float32).contiguous()
+                                    device=dev, dtype=torch.float32, chunk=2048).contiguous()
         T = hs.haar_forward(w)
         top = torch.topk(T.abs(), K, dim=1).indices
         top, _ = torch.sort(top, dim=1)
@@ -137,20 +168,242 @@ def prepare_c1(hs, dev, rank: int):
     idx16 = idx.to(torch.int32).to(torch.int16).contiguous()
     params = torch.tensor(sc["params"], dtype=torch.float64, device=dev)
     plan = hs.Plan(H, W, C, kind=hs.HAAR_SHIFT_TRANSLATE, max_shifts=S, out_layout=hs.HAAR_LAYOUT_KSC)
-    tr = hs.Transport(hs.HAAR_T_CSR_F32_U16, V, 0, vals.reshape(-1).contiguous(), idx16.reshape(-1), rowptr)
+    csr = hs.Transport(hs.HAAR_T_CSR_F32_U16, V, 0, vals.reshape(-1).contiguous(), idx16.reshape(-1), rowptr)
+    tr = hs.haar_transport_group(V, H * W, rowptr, idx16.reshape(-1), vals.reshape(-1).contiguous())
+    del vals, idx
     lighting = torch.empty((H * W, S, C), dtype=torch.float32, device=dev)
     radiance = torch.empty((V, S, C), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
-    return dict(sc=sc, H=H, W=W, C=C, S=S, V=V, K=K, L=L, params=params, plan=plan, tr=tr,
-                lighting=lighting, radiance=radiance)
+    return dict(sc=sc, H=H, W=W, C=C, S=S, V=V, K=K, L=L, params=params, plan=plan, tr=tr, csr=csr,
+                union=int(tr.rowptr[-1].item()), lighting=lighting, radiance=radiance)
 
 
 def algorithmic_bytes(wl):
-    """Bytes a kernel must move at least, per launch."""
+    """Bytes a kernel must move at least, per launch: its stored input read
+    once, the lighting read once, its output written once."""
     V, K, S, C, N = wl["V"], wl["K"], wl["S"], wl["C"], wl["H"] * wl["W"]
-    shade = V * K * 4 + V * K * 2 + (V + 1) * 4 + N * S * C * 4 + V * S * C * 4
+    U, G = wl["union"], (wl["V"] + 7) // 8
+    gcsr = U * (8 * 4 + 2) + (G + 1) * 4 + N * S * C * 4 + V * S * C * 4
+    csr = V * K * 4 + V * K * 2 + (V + 1) * 4 + N * S * C * 4 + V * S * C * 4
     shift = C * N * 4 + S * C * N * 4
-    return {"k_shade_csr_f32": shade, "k_shift": shift}
+    return {"k_shade_gcsr_f32": gcsr, "k_shade_csr_f32": csr, "k_shift": shift}
+
+
+# ----------------------------------------------------------------- other §8 rows
+
+def _timeit(fn, reps, flush, stream):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median([a.elapsed_time(b) for a, b in evs])
+
+
+def _bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = json.load(open(p)) if os.path.exists(p) else {}
+    return d.get("bf16_tflops", 1900.0), d.get("hbm_gbs", 6800.0)
+
+
+def _glossy_transport(hs, sc, dev, bins=16, K=512, chunk=8192):
+    """View-binned top-K glossy transport of every (vertex, bin) on the GPU:
+    Phong transfer on the 64x128 grid, projected by haar_forward (the lowest
+    8192 coefficients of the 256x512 map), top-K per row, sorted by index."""
+    import numpy as np
+    import torch
+    import synth
+    V = sc["V"]
+    view = synth.bin_view_world(sc["nrm"], bins).reshape(-1, 3)
+    rows = V * bins
+    vals = torch.empty((rows, K), dtype=torch.float16, device=dev)
+    idx = torch.empty((rows, K), dtype=torch.int32, device=dev)
+    absum = torch.zeros(8192, dtype=torch.float64, device=dev)
+    for a in range(0, rows, chunk):
+        b = min(rows, a + chunk)
+        vi = np.arange(a, b) // bins
+        w = synth.transport_weights(sc["pos"][vi], sc["nrm"][vi], sc["occ_c"], sc["occ_r"], 64, 128,
+                                    view=view[a:b], expo=sc["expo"][vi], device=dev, dtype=torch.float32,
+                                    chunk=chunk)
+        T = hs.haar_forward(w.contiguous(), scale=0.25)
+        absum += T.abs().sum(0).double()
+        top = torch.topk(T.abs(), K, dim=1).indices
+        top, _ = torch.sort(top, dim=1)
+        idx[a:b] = top.to(torch.int32)
+        vals[a:b] = torch.gather(T, 1, top).to(torch.float16)
+        del w, T
+    return vals.reshape(V, bins, K), idx.reshape(V, bins, K), absum
+
+
+def measure_rows(hs, dev, flush, only=None):
+    """Per-row measurements of the rest of the hot path; ``only`` restricts
+    them to the named rows (for profiling one kernel)."""
+    import numpy as np
+    import torch
+    import synth
+    stream = torch.cuda.current_stream(dev)
+    bf16_peak, hbm = _bf16_peak()
+    rows = {}
+
+    def want(name):
+        return only is None or name in only
+
+    # S2 / S4 roofline: 4096 translations of the RGB 128x256 map, full FP32 output (1.6 GB)
+    if want("translation_shift_batch"):
+        sc1 = synth.scene(1, V=1)
+        L1 = hs.haar_forward(torch.tensor(sc1["light"], dtype=torch.float32, device=dev))
+        S = 4096
+        prm = torch.tensor(synth.translations(synth.rng_for(1, 7), S, 256.0, 256.0), dtype=torch.float64, device=dev)
+        plan = hs.Plan(128, 256, 3, max_shifts=S)
+        out = torch.empty(plan.out_shape(S), dtype=torch.float32, device=dev)
+        ms = _timeit(lambda: hs.haar_shift(plan, L1, prm, out), 5, flush, stream)
+        byt = 4 * 3 * 32768 * (S + 1)
+        rows["translation_shift_batch"] = {"what": "haar_shift, 4096 fractional shifts of RGB 128x256, FP32 SCK",
+                                           "ms": ms, "achieved_gbs": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm,
+                                           "bound": "hbm", "algorithmic_bytes": byt}
+        plan.close()
+        del out
+
+    # S3 roofline: 512 rotations of the RGB 256x512 map, full FP32 output (805 MB)
+    if want("rotation_shift_batch"):
+        sc2 = synth.scene(2, V=1)
+        L2 = hs.haar_forward(torch.tensor(sc2["light"], dtype=torch.float32, device=dev))
+        S = 512
+        eul = torch.tensor(synth.euler_angles(synth.rng_for(2, 7), S), dtype=torch.float64, device=dev)
+        plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S)
+        out = torch.empty(plan.out_shape(S), dtype=torch.float32, device=dev)
+        ms = _timeit(lambda: hs.haar_shift(plan, L2, eul, out), 5, flush, stream)
+        byt = 4 * 3 * 131072 * (S + 1)
+        rows["rotation_shift_batch"] = {"what": "haar_shift, 512 rotations of RGB 256x512, FP32 SCK",
+                                        "ms": ms, "achieved_gbs": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm,
+                                        "bound": "alu (atan2 coordinates) / hbm", "algorithmic_bytes": byt}
+        plan.close()
+        del out
+
+    # c2 frame: 64 rotations -> bf16 hi/lo lowest 4096 -> tcgen05 contraction for 200k vertices
+    if want("c2_dense_tc"):
+        sc2 = synth.scene(2)
+        V, K, S = sc2["V"], 4096, 64
+        T = torch.empty((V, K), dtype=torch.bfloat16, device=dev)
+        for a in range(0, V, 16384):
+            b = min(V, a + 16384)
+            w = synth.transport_weights(sc2["pos"][a:b], sc2["nrm"][a:b], sc2["occ_c"], sc2["occ_r"], 64, 128,
+                                        device=dev, dtype=torch.float32, chunk=8192).contiguous()
+            T[a:b] = hs.haar_forward(w, scale=0.25)[:, :K].to(torch.bfloat16)
+            del w
+        eul = torch.tensor(sc2["params"], dtype=torch.float64, device=dev)
+        plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_coeffs=K,
+                       out_type=hs.HAAR_OUT_BF16_HILO)
+        lit = torch.empty(plan.out_shape(S), dtype=torch.bfloat16, device=dev)
+        tr = hs.Transport(hs.HAAR_T_DENSE_BF16, V, K, T)
+        R = torch.empty((V, S, 3), dtype=torch.float32, device=dev)
+        hs.haar_shift(plan, L2, eul, lit)
+        ms_gemm = _timeit(lambda: hs.shade_vertices(plan, tr, lit, S, R), 10, flush, stream)
+        ms_frame = _timeit(lambda: (hs.haar_shift(plan, L2, eul, lit), hs.shade_vertices(plan, tr, lit, S, R)), 10,
+                           flush, stream)
+        flops = 2.0 * 2.0 * V * K * S * 3
+        gbytes = (2.0 * V * K + 4.0 * V * S * 3 + 2 * 2.0 * S * 3 * K)
+        rows["c2_dense_tc"] = {"what": "c2 frame: 64 rotations + tcgen05 bf16 contraction T[200000x4096] x (Lhi+Llo)[4096x192]",
+                               "frame_ms": ms_frame, "value": V * S / ms_frame / 1e3, "unit": UNIT,
+                               "kernel": "k_dense_bf16", "kernel_ms": ms_gemm,
+                               "achieved_tflops": flops / ms_gemm / 1e9, "peak_tflops": bf16_peak,
+                               "frac_tensor": flops / ms_gemm / 1e9 / bf16_peak,
+                               "achieved_gbs": gbytes / ms_gemm / 1e6, "frac_hbm": gbytes / ms_gemm / 1e6 / hbm,
+                               "flops_counted": "2 x (2 V K S C): hi and lo products"}
+        plan.close()
+        del T, lit, R, tr
+
+    # c3 frame: view bins + 32 rotations (FP32 SKC) + view-binned top-512 FP16 shading
+    c3 = None
+    if want("c3_bincsr") or want("c4_surrogate") or want("surrogate_training"):
+        sc3 = synth.scene(3)
+        V, S = sc3["V"], sc3["S"]
+        vals, idx, absum = _glossy_transport(hs, sc3, dev)
+        f = lambda x: torch.tensor(x, dtype=torch.float32, device=dev)
+        pos, nrm, cams, dirs = f(sc3["pos"]), f(sc3["nrm"]), f(sc3["cams"]), f(synth.view_bin_dirs(16))
+        eul3 = torch.tensor(sc3["params"], dtype=torch.float64, device=dev)
+        L3 = hs.haar_forward(torch.tensor(sc3["light"], dtype=torch.float32, device=dev))
+        plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_layout=hs.HAAR_LAYOUT_SKC)
+        lit = torch.empty(plan.out_shape(S), dtype=torch.float32, device=dev)
+        bins = torch.empty((S, V), dtype=torch.uint8, device=dev)
+        R = torch.empty((V, S, 3), dtype=torch.float32, device=dev)
+        tr = hs.Transport(hs.HAAR_T_BINCSR_F16_U32, V, 512, vals, idx, bins=16, bin_of=bins)
+
+        def c3_frame():
+            hs.haar_view_bins(pos, nrm, cams, dirs, bins)
+            hs.haar_shift(plan, L3, eul3, lit)
+            hs.shade_vertices(plan, tr, lit, S, R)
+        ms_frame = _timeit(c3_frame, 10, flush, stream)
+        plain_c3 = V * S / ms_frame / 1e3
+        if want("c3_bincsr"):
+            ms_shade = _timeit(lambda: hs.shade_vertices(plan, tr, lit, S, R), 10, flush, stream)
+            distinct = int(torch.unique(bins.to(torch.int64) + 16 * torch.arange(V, device=dev)[None, :]).numel())
+            byt = distinct * 512 * 6 + V * S * 3 * 4 + S * 8192 * 3 * 4
+            rows["c3_bincsr"] = {"what": "c3 frame: view bins + 32 rotations + top-512 FP16 view-binned shading, 100k vertices",
+                                 "frame_ms": ms_frame, "value": plain_c3, "unit": UNIT,
+                                 "kernel": "k_shade_bincsr_f16", "kernel_ms": ms_shade,
+                                 "achieved_gbs": byt / ms_shade / 1e6, "frac_hbm": byt / ms_shade / 1e6 / hbm,
+                                 "distinct_vertex_bins": distinct}
+        del vals, idx, tr, R
+        c3 = True
+
+    if c3 and (want("c4_surrogate") or want("surrogate_training")):
+        # c4 frame: the same 32 rotations, transport from the surrogate (random-init
+        # weights, index set = 512 largest mean |T| of the c3 transports), fused shading
+        K = 512
+        isel = torch.sort(torch.topk(absum, K).indices).values.to(torch.int32)
+        mu = torch.zeros(K, dtype=torch.float32, device=dev)
+        sg = torch.full((K,), 1e-3, dtype=torch.float32, device=dev)
+        net = hs.Surrogate(max_batch=8192, max_rows=262144, max_groups=S)
+        rng = np.random.default_rng(4)
+        flat = []
+        for fi, fo in ((320, 256), (256, 256), (256, 256), (256, 256), (256, 512)):
+            flat += [rng.standard_normal(fo * fi) * math.sqrt(2.0 / fi), np.zeros(fo)]
+        net.set_params(torch.tensor(np.concatenate(flat), dtype=torch.float32, device=dev))
+        R4 = torch.empty((V, S, 3), dtype=torch.float32, device=dev)
+        N3 = 131072
+        strides = (N3 * 3, 1, 3)
+        if want("c4_surrogate"):
+            def c4_frame():
+                hs.haar_shift(plan, L3, eul3, lit)
+                net.shade(pos, nrm, cams, mu, sg, isel, lit, 3, strides, R4)
+            ms_frame = _timeit(c4_frame, 5, flush, stream)
+            ms_mlp = _timeit(lambda: net.shade(pos, nrm, cams, mu, sg, isel, lit, 3, strides, R4), 5, flush, stream)
+            mlp_flops = 2.0 * V * S * (320 * 256 + 3 * 256 * 256 + 256 * 3)
+            rows["c4_surrogate"] = {"what": "c4 frame: 32 rotations + surrogate transport (4x256 GELU MLP, bf16 tcgen05) "
+                                            "fused with shading",
+                                    "frame_ms": ms_frame, "value": V * S / ms_frame / 1e3, "unit": UNIT,
+                                    "kernel": "haar_mlp_shade", "kernel_ms": ms_mlp,
+                                    "achieved_tflops": mlp_flops / ms_mlp / 1e9,
+                                    "frac_tensor": mlp_flops / ms_mlp / 1e9 / bf16_peak,
+                                    "vs_plain_c3_frame": (V * S / ms_frame / 1e3) / plain_c3,
+                                    "weights": "random init (throughput only)"}
+        if want("surrogate_training"):
+            # S8: one Adam training step on a batch of 8192
+            B = 8192
+            raw = torch.randn((B, 9), dtype=torch.float32, device=dev)
+            tgt = torch.randn((B, 512), dtype=torch.float32, device=dev)
+            ms_eager = _timeit(lambda: net.train_step(raw, tgt, 1e-4), 10, flush, stream)
+            graph, _ = net.capture_train_step(raw, tgt, 1e-4)
+            ms_train = _timeit(graph.replay, 10, flush, stream)
+            tflops = 3.0 * 2.0 * B * (320 * 256 + 3 * 256 * 256 + 256 * 512) / ms_train / 1e9
+            rows["surrogate_training"] = {"what": "haar_mlp_train_step, batch 8192 (forward, backward, Adam), "
+                                                  "replayed from a CUDA graph",
+                                          "ms": ms_train, "eager_ms": ms_eager, "samples_per_s": B / ms_train * 1e3,
+                                          "achieved_tflops": tflops, "frac_tensor": tflops / bf16_peak}
+        net.close()
+    if c3:
+        plan.close()
+    return rows
 
 
 class Clocks:
@@ -244,6 +497,10 @@ def main():
     _build.build()
     hs.lib()
 
+    if args.only:
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"rows": measure_rows(hs, dev, flush, set(args.only.split(",")))}), flush=True)
+        return 0
     wl = prepare_c1(hs, dev, rank)
     plan, tr = wl["plan"], wl["tr"]
     stream = torch.cuda.current_stream(dev)
@@ -277,14 +534,10 @@ def main():
     clocks.start()
     step_ms = timed(step, args.steps)
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
     units = wl["V"] * wl["S"] * world
-    value = units / (ms_per_step * 1e-3) / 1e6
+    value = whole_job_value(wl["V"] * wl["S"], ms_per_step, world)
 
     # per-kernel durations for the roofline (same stream, same flush discipline)
     shade_ms = timed(lambda: hs.shade_vertices(plan, tr, wl["lighting"], wl["S"], wl["radiance"]), args.steps)
@@ -295,16 +548,19 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    csr_ms = timed(lambda: hs.shade_vertices(plan, wl["csr"], wl["lighting"], wl["S"], wl["radiance"]), args.steps)
+    csr_avg = statistics.mean(csr_ms)
     if shade_avg >= shift_avg:
-        kname, kms = "k_shade_csr_f32", shade_avg
+        kname, kms = "k_shade_gcsr_f32", shade_avg
     else:
         kname, kms = "k_shift", shift_avg
     achieved = ab[kname] / (kms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic_record(kname), "kernel": kname, "peak_source": peak_src,
                 "algorithmic_bytes": ab[kname], "kernel_ms": kms,
-                "other_kernels_ms": {"k_setup+k_shift": shift_avg} if kname != "k_shift" else
-                {"k_shade_csr_f32": shade_avg}}
+                "other_kernels_ms": {"k_setup+k_shift": shift_avg, "k_shade_gcsr_f32": shade_avg},
+                "plain_csr_kernel": {"kernel": "k_shade_csr_f32", "ms": csr_avg,
+                                     "achieved_gbs": ab["k_shade_csr_f32"] / (csr_avg * 1e-3) / 1e9}}
 
     # end to end through the public API with host buffers
     L_host = wl["L"].cpu().pin_memory()
@@ -322,14 +578,14 @@ def main():
     for _ in range(3):
         e2e_step()
     e2e_ms = timed(e2e_step, args.steps)
-    e2e_tot = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_tot], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = units / (e2e_tot / args.steps * 1e-3) / 1e6
+    e2e_tot = max_over_ranks(sum(e2e_ms), dev)
+    e2e_value = whole_job_value(wl["V"] * wl["S"], e2e_tot / args.steps, world)
     h2d = L_host.numel() * 4 + p_host.numel() * 8
     d2h = R_host.numel() * 4
+
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = measure_rows(hs, dev, flush)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -341,7 +597,7 @@ def main():
                            "parallelism": f"{world} independent vertex shards (no collective)"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": 3 * args.steps, "clocks": clk}
+                "gpu_launches": 3 * args.steps, "clocks": clk, "rows": rows}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

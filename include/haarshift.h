@@ -165,8 +165,13 @@ typedef enum {
   HAAR_T_DENSE_F32 = 0,     /* vals [V][K] float32, lowest K coefficients */
   HAAR_T_DENSE_BF16 = 1,    /* vals [V][K] bfloat16, lowest K coefficients */
   HAAR_T_CSR_F32_U16 = 2,   /* vals float32, idx uint16, rowptr int32 [V+1] */
-  HAAR_T_BINCSR_F16_U32 = 3 /* vals [V][bins][K] binary16, idx [V][bins][K] uint32,
+  HAAR_T_BINCSR_F16_U32 = 3, /* vals [V][bins][K] binary16, idx [V][bins][K] uint32,
                                bin_of [S][V] uint8 selects the bin of (s, v) */
+  HAAR_T_GCSR_F32_U16 = 4    /* vertex-group CSR made by haar_transport_group: groups of
+                               8 consecutive vertices share one sorted union index list
+                               idx (uint16) with values [nnz][8] float32 (0 where a
+                               vertex lacks the coefficient); rowptr = group offsets
+                               [ceil(V/8) + 1] int32 */
 } haar_transport_kind_t;
 
 typedef struct {
@@ -189,7 +194,8 @@ typedef struct {
  *                    K % 64 == 0 (tcgen05 tensor-core GEMM, FP32 accumulate,
  *                    T x L_hi + T x L_lo);
  *   CSR_F32_U16      with F32  lighting, layout KSC (S*C % 4 == 0);
- *   BINCSR_F16_U32   with F32  lighting, layout SKC.
+ *   BINCSR_F16_U32   with F32  lighting, layout SKC;
+ *   GCSR_F32_U16     with F32  lighting, layout KSC (S*C % 4 == 0).
  * radiance: [V][S][C] float32, overwritten. */
 HAAR_API haar_status_t shade_vertices(haar_shift_plan_t plan, const haar_transport_desc_t* transport,
                              const void* lighting, int S, float* radiance, void* stream);
@@ -199,6 +205,20 @@ HAAR_API haar_status_t shade_vertices(haar_shift_plan_t plan, const haar_transpo
 HAAR_API haar_status_t shade_batch(haar_shift_plan_t plan, const float* coeffs_in, const double* params,
                           int S, const haar_transport_desc_t* transport, float* radiance,
                           void* stream);
+
+/* Repack top-K CSR transport (rows sorted by index, rowptr int32 [V+1],
+ * idx uint16, vals float32) into the vertex-group CSR of HAAR_T_GCSR_F32_U16:
+ * the union of the indices of every 8 consecutive rows, sorted, with the
+ * values of each row at its union positions (0 elsewhere).  A storage form
+ * of the top-K (non-linear) approximation cited in Sec. "Haar-domain
+ * methods": the double product is unchanged, each lighting row gathered
+ * serves 8 vertices.  N: coefficients per map (<= 65536; indices >= N are
+ * dropped).  gptr [ceil(V/8) + 1] int32 (device) receives the group offsets;
+ * gptr[ceil(V/8)] is the total.  Call once with gidx = gvals = NULL to get
+ * gptr, then again with gidx [total] uint16 and gvals [total][8] float32. */
+HAAR_API haar_status_t haar_transport_group(int V, int N, const int32_t* rowptr, const uint16_t* idx,
+                                            const float* vals, int32_t* gptr, uint16_t* gidx, float* gvals,
+                                            void* stream);
 
 /* View-bin selection for view-dependent transport (the paper's per-pixel
  * "BRDF tile id" of the rotation input pass, Sec. "Experimental results"):

@@ -43,13 +43,14 @@ HAAR_T_DENSE_F32 = 0
 HAAR_T_DENSE_BF16 = 1
 HAAR_T_CSR_F32_U16 = 2
 HAAR_T_BINCSR_F16_U32 = 3
+HAAR_T_GCSR_F32_U16 = 4
 
 EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward",
            "haar_inverse", "shade_vertices", "shade_batch", "haar_view_bins",
            "haar_last_error", "haar_version", "haar_mlp_param_count", "haar_mlp_create",
            "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params", "haar_mlp_forward",
            "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status",
-           "haar_shift_noalloc")
+           "haar_shift_noalloc", "haar_transport_group")
 
 
 class HaarShiftDesc(ctypes.Structure):
@@ -91,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.shade_vertices.argtypes = [vp, ctypes.POINTER(HaarTransportDesc), vp, i, vp, vp]
     L.shade_batch.argtypes = [vp, vp, vp, i, ctypes.POINTER(HaarTransportDesc), vp, vp]
     L.haar_view_bins.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp]
+    L.haar_transport_group.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp]
+    L.haar_transport_group.restype = st
     for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_shift_noalloc", "haar_forward", "haar_inverse",
                  "shade_vertices", "shade_batch", "haar_view_bins"):
         getattr(L, name).restype = st
@@ -107,7 +110,8 @@ def lib() -> ctypes.CDLL:
     L.haar_mlp_shade.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, i, ll, ll, ll, vp, vp]
     L.haar_mlp_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     for name in ("haar_mlp_create", "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params",
-                 "haar_mlp_forward", "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status"):
+                 "haar_mlp_forward", "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status",
+           "haar_shift_noalloc", "haar_transport_group"):
         getattr(L, name).restype = st
     L.haar_last_error.restype = ctypes.c_char_p
     L.haar_last_error.argtypes = []
@@ -276,6 +280,22 @@ def shade_batch(plan: Plan, coeffs_in, params, transport: Transport, radiance=No
     return radiance
 
 
+def haar_transport_group(V, N, rowptr, idx, vals, stream=None):
+    """Vertex-group CSR (Transport of kind HAAR_T_GCSR_F32_U16) from top-K CSR."""
+    import torch
+    G = (V + 7) // 8
+    gptr = torch.empty(G + 1, dtype=torch.int32, device=rowptr.device)
+    st = _stream(stream)
+    _check(lib().haar_transport_group(V, N, _dev(rowptr, torch.int32, "rowptr"), _dev(idx, None, "idx"),
+                                      _dev(vals, torch.float32, "vals"), gptr.data_ptr(), None, None, st))
+    total = int(gptr[-1].item())
+    gidx = torch.empty(max(total, 1), dtype=torch.int16, device=rowptr.device)
+    gvals = torch.empty((max(total, 1), 8), dtype=torch.float32, device=rowptr.device)
+    _check(lib().haar_transport_group(V, N, rowptr.data_ptr(), idx.data_ptr(), vals.data_ptr(), gptr.data_ptr(),
+                                      gidx.data_ptr(), gvals.data_ptr(), st))
+    return Transport(HAAR_T_GCSR_F32_U16, V, 0, gvals, gidx, gptr)
+
+
 def haar_view_bins(pos, nrm, cams, bin_dirs, out=None, stream=None):
     """bin_of [S][V] uint8: the view bin of every (s, v)."""
     import torch
@@ -344,6 +364,16 @@ class Surrogate:
                                          _dev(target, torch.float32, "target"), raw.shape[0], float(lr),
                                          loss.data_ptr(), _stream(stream)))
         return loss
+
+    def capture_train_step(self, raw, target, lr):
+        """A CUDA graph of one training step on the fixed buffers raw / target
+        (copy each new batch into them, then replay()); returns (graph, loss)."""
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device=raw.device)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.train_step(raw, target, lr, loss)
+        return graph, loss
 
     def shade(self, pos, nrm, cams, mu, sigma, idx, lighting, C, strides, radiance=None, stream=None):
         """radiance [V][S][C]; strides = (st_s, st_c, st_k) of the float32 lighting."""

@@ -101,7 +101,8 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
   if (!p) return set_error(HAAR_ERR_NOMEM, "haar_shift_plan: host allocation failed");
   memset(p, 0, sizeof(*p));
   p->desc = *d;
-  p->geo = make_geometry(d->height, d->width, d->channels, d->boundary);
+  p->geo = make_geometry(d->height, d->width, d->channels, d->boundary,
+                         choose_tile(d->height, d->width, d->channels, d->max_shifts));
   p->K = d->out_coeffs ? d->out_coeffs : (int)N;
   cudaGetDevice(&p->device);
   const Geometry& g = p->geo;
@@ -231,6 +232,16 @@ static haar_status_t shade_impl(haar_shift_plan_t p, const haar_transport_desc_t
       if (p->K > 65536) return set_error(HAAR_ERR_UNSUPPORTED, "%s: uint16 indices cover at most 65536 coefficients", who);
       return launch_shade_csr_f32((const float*)t->vals, (const uint16_t*)t->idx, t->rowptr, t->V, (const float*)L,
                                   p->K, ncols, R, st);
+    case HAAR_T_GCSR_F32_U16:
+      if (ot != HAAR_OUT_F32 || lay != HAAR_LAYOUT_KSC)
+        return set_error(HAAR_ERR_UNSUPPORTED, "%s: GCSR_F32_U16 needs F32 lighting in KSC layout", who);
+      if (ncols % 4 != 0) return set_error(HAAR_ERR_UNSUPPORTED, "%s: GCSR needs S*C %% 4 == 0", who);
+      if (t->idx == nullptr || t->rowptr == nullptr) return set_error(HAAR_ERR_INVALID_ARG, "%s: GCSR needs idx and rowptr", who);
+      if (!aligned(L, 16) || !aligned(R, 16))
+        return set_error(HAAR_ERR_INVALID_ARG, "%s: lighting and radiance must be 16-byte aligned", who);
+      if (p->K > 65536) return set_error(HAAR_ERR_UNSUPPORTED, "%s: uint16 indices cover at most 65536 coefficients", who);
+      return launch_shade_gcsr_f32((const float*)t->vals, (const uint16_t*)t->idx, t->rowptr, t->V, (const float*)L,
+                                   p->K, ncols, R, st);
     case HAAR_T_BINCSR_F16_U32:
       if (ot != HAAR_OUT_F32 || lay != HAAR_LAYOUT_SKC)
         return set_error(HAAR_ERR_UNSUPPORTED, "%s: BINCSR_F16_U32 needs F32 lighting in SKC layout", who);
@@ -262,6 +273,16 @@ haar_status_t shade_batch(haar_shift_plan_t p, const float* cin, const double* p
   r = launch_shift(p, cin, S, p->light, st);
   if (r != HAAR_OK) return r;
   return shade_impl(p, t, p->light, S, R, st, "shade_batch");
+}
+
+haar_status_t haar_transport_group(int V, int N, const int32_t* rowptr, const uint16_t* idx, const float* vals,
+                                   int32_t* gptr, uint16_t* gidx, float* gvals, void* stream) {
+  HS_ENTRY("haar_transport_group");
+  if (V < 0 || N < 1 || N > 65536) return set_error(HAAR_ERR_INVALID_ARG, "haar_transport_group: V=%d N=%d", V, N);
+  if (V == 0) return HAAR_OK;
+  if (!rowptr || !idx || !gptr || (gidx == nullptr) != (gvals == nullptr) || (gidx && !vals))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_transport_group: null pointer");
+  return launch_gcsr_pack(V, N, rowptr, idx, vals, gptr, gidx, gvals, (cudaStream_t)stream);
 }
 
 haar_status_t haar_view_bins(int V, int S, int bins, const float* pos, const float* nrm, const float* cams,

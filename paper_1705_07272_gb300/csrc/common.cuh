@@ -33,14 +33,21 @@ struct Geometry {
   long long N;               // H * W
 };
 
-static inline Geometry make_geometry(int H, int W, int C, int boundary) {
+// Tile side: 64 x 64 output tiles unless that leaves too few CTAs for the
+// machine (small maps with few shifts), then 32 x 32.
+static inline int choose_tile(int H, int W, int C, int S) {
+  const long long t64 = (H >= 64) ? (long long)(H / 64) * (W / 64) : 1;
+  return (t64 * C * S >= 640) ? 64 : 32;
+}
+
+static inline Geometry make_geometry(int H, int W, int C, int boundary, int tile = 64) {
   Geometry g;
   g.H = H; g.W = W; g.C = C; g.boundary = boundary;
   int n = 0;
   while ((1 << n) < H) ++n;
   g.n = n;
   g.q = W / H;
-  g.T = H < 64 ? H : 64;
+  g.T = H < tile ? H : tile;
   int lt = 0;
   while ((1 << lt) < g.T) ++lt;
   g.Lt = lt;
@@ -95,6 +102,10 @@ haar_status_t launch_shade_csr_f32(const float* vals, const uint16_t* idx, const
 haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,
                                       int V, int bins, int K, int S, int C, const float* L,
                                       long long NL, float* R, cudaStream_t st);
+haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, const int32_t* gptr, int V,
+                                    const float* L, int NL, int ncols, float* R, cudaStream_t st);
+haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16_t* idx, const float* vals,
+                               int32_t* gptr, uint16_t* gidx, float* gvals, cudaStream_t st);
 haar_status_t launch_view_bins(int V, int S, int bins, const float* pos, const float* nrm,
                                const float* cams, const float* bin_dirs, uint8_t* bin_of,
                                cudaStream_t st);

@@ -152,41 +152,61 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
   } else {
     const int quarter = warp & 3;
     const int m = tm * BM + quarter * 32 + lane;
+    // bf16 outputs are staged per warp (32 rows x BN, rows padded by 16 bytes)
+    // in the stage ring, free once the accumulator is complete, and written
+    // back one row per warp instruction (coalesced)
+    const uint32_t pitch = (uint32_t)BN * 2 + 16;
+    uint8_t* stage = smem_raw + (base - smem_u32(smem_raw)) + (size_t)quarter * 32 * pitch;
     if (mbar_wait(smem_u32(&bars.tfull), 0, status, abort_flag)) {
       fence_after();
       const uint32_t t_row = tmem + ((uint32_t)(quarter * 32) << 16);
       float acc_c[4] = {0.f, 0.f, 0.f, 0.f};
       int grp = 0;
       if (EPI == EPI_SHADE) grp = (m + e.row0) / e.rows_per_group;
+      const bool row_ok = m < e.M;
       for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
         tmem_ld16(t_row + (uint32_t)c0, v);
         const int n0 = tn * BN + c0;
-        if (m >= e.M) continue;
         if (EPI == EPI_F32) {
+          if (row_ok) {
+            float* dst = e.out_f32 + (long long)m * e.ld_f32 + n0;
+            if (n0 + 16 <= e.N && (e.ld_f32 & 3) == 0) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + i;
-            if (n < e.N) e.out_f32[(long long)m * e.ld_f32 + n] = v[i] + (e.bias ? e.bias[n] : 0.0f);
-          }
-        } else if (EPI == EPI_BIAS_GELU) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + i;
-            if (n < e.N) {
-              const float z = v[i] + e.bias[n];
-              if (e.out_f32) e.out_f32[(long long)m * e.ld_f32 + n] = z;
-              e.out_bf16[(long long)m * e.ld_bf16 + n] = __float2bfloat16_rn(gelu(z));
+              for (int i = 0; i < 16; i += 4)
+                *reinterpret_cast<float4*>(dst + i) =
+                    make_float4(v[i] + (e.bias ? e.bias[n0 + i] : 0.f), v[i + 1] + (e.bias ? e.bias[n0 + i + 1] : 0.f),
+                                v[i + 2] + (e.bias ? e.bias[n0 + i + 2] : 0.f), v[i + 3] + (e.bias ? e.bias[n0 + i + 3] : 0.f));
+            } else {
+              for (int i = 0; i < 16; ++i)
+                if (n0 + i < e.N) dst[i] = v[i] + (e.bias ? e.bias[n0 + i] : 0.0f);
             }
           }
-        } else if (EPI == EPI_GELU_BWD) {
+        } else if (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD) {
+          uint32_t packed[8];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + i;
-            if (n < e.N)
-              e.out_bf16[(long long)m * e.ld_bf16 + n] =
-                  __float2bfloat16_rn(v[i] * gelu_grad(e.zprev[(long long)m * e.ld_zprev + n]));
+          for (int i = 0; i < 16; i += 2) {
+            float h0, h1;
+            if (EPI == EPI_BIAS_GELU) {
+              const float z0 = v[i] + e.bias[min(n0 + i, e.N - 1)];
+              const float z1 = v[i + 1] + e.bias[min(n0 + i + 1, e.N - 1)];
+              if (e.out_f32 && row_ok) {
+                if (n0 + i < e.N) e.out_f32[(long long)m * e.ld_f32 + n0 + i] = z0;
+                if (n0 + i + 1 < e.N) e.out_f32[(long long)m * e.ld_f32 + n0 + i + 1] = z1;
+              }
+              h0 = gelu(z0);
+              h1 = gelu(z1);
+            } else {
+              const float* zp = e.zprev + (long long)(row_ok ? m : 0) * e.ld_zprev;
+              h0 = v[i] * gelu_grad(zp[min(n0 + i, e.N - 1)]);
+              h1 = v[i + 1] * gelu_grad(zp[min(n0 + i + 1, e.N - 1)]);
+            }
+            __nv_bfloat162 hb = __floats2bfloat162_rn(h0, h1);
+            packed[i >> 1] = *reinterpret_cast<uint32_t*>(&hb);
           }
+          uint4* sp = reinterpret_cast<uint4*>(stage + (size_t)lane * pitch + (size_t)c0 * 2);
+          sp[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          sp[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         } else {  // EPI_SHADE: fold gelu(z) against the per-group effective output weights
           const float* W = e.weff + (long long)grp * e.N * e.C;
 #pragma unroll
@@ -201,7 +221,18 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
           }
         }
       }
-      if (EPI == EPI_SHADE && m < e.M) {
+      if (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD) {
+        __syncwarp();
+        const int ncol = min(BN, e.N - tn * BN);            // valid columns of this tile (multiple of 8)
+        for (int r = 0; r < 32; ++r) {
+          const int mr = tm * BM + quarter * 32 + r;
+          if (mr >= e.M) break;
+          for (int cb = lane * 8; cb < ncol; cb += 256)
+            *reinterpret_cast<uint4*>(e.out_bf16 + (long long)mr * e.ld_bf16 + tn * BN + cb) =
+                *reinterpret_cast<const uint4*>(stage + (size_t)r * pitch + (size_t)cb * 2);
+        }
+      }
+      if (EPI == EPI_SHADE && row_ok) {
         const int row = m + e.row0;
         const int s = row / e.rows_per_group, vv = row - s * e.rows_per_group;
         for (int c = 0; c < e.C; ++c)
@@ -315,9 +346,13 @@ __global__ void k_colsum(const __nv_bfloat16* __restrict__ dz, int B, int N, flo
   }
 }
 
+// One Adam step; the step count lives on the device (read here, advanced by
+// k_pack) so captured training steps replay correctly.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                       const int* __restrict__ step) {
+  const float t = (float)(*step + 1);
+  const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
@@ -329,8 +364,10 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 }
 
 // bf16 copies of every weight matrix ([out][in]) and of its transpose ([in][out])
-__global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt) {
+__global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt,
+                       int* step, int advance) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (advance && i == 0) *step += 1;
   long long off = 0;
   for (int l = 0; l < N_LAYERS; ++l) {
     const long long sz = (long long)fan_out(l) * fan_in(l);
@@ -391,7 +428,6 @@ struct haar_mlp_s {
   float* v;           // Adam second moments
   __nv_bfloat16* wb;  // bf16 weights, [out][in] per layer
   __nv_bfloat16* wt;  // bf16 transposed weights, [in][out] per layer
-  int adam_t;
   // training buffers (max_batch rows)
   __nv_bfloat16* X;   // [B][320]
   __nv_bfloat16* h[4];// [B][256]
@@ -403,6 +439,7 @@ struct haar_mlp_s {
   __nv_bfloat16* tA;  // transpose scratch [512][B]
   __nv_bfloat16* tB;  // transpose scratch [320][B]
   float* loss;        // [1]
+  int* step;          // [1] Adam step count
   // inference buffers (max_rows rows)
   __nv_bfloat16* iX;  // [rows][320]
   __nv_bfloat16* ih0; // [rows][256]
@@ -438,10 +475,16 @@ static haar_status_t gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B,
   CUtensorMap mA, mB;
   if (!encode_2d(&mA, A, (uint64_t)K, (uint64_t)M, BK, BM) || !encode_2d(&mB, B, (uint64_t)K, (uint64_t)N, BK, (uint32_t)BN))
     return set_error(HAAR_ERR_CUDA, "mlp gemm: cuTensorMapEncodeTiled failed");
+  if ((EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD) && (N % 8) != 0)
+    return set_error(HAAR_ERR_UNSUPPORTED, "mlp gemm: bf16 outputs need N %% 8 == 0");
   const size_t stage = (size_t)BM * BK * 2 + (size_t)BN * BK * 2;
-  int stages = (int)(SMEM_BUDGET / stage);
-  if (stages > MAX_STAGES) stages = MAX_STAGES;
-  const size_t smem = (size_t)stages * stage + 1024;
+  // two stages (two CTAs per SM overlap one's epilogue with the other's
+  // main loop); the bf16 epilogue stages its rows in the same memory
+  int stages = K / BK < 2 ? 1 : 2;
+  size_t ring = (size_t)stages * stage;
+  const size_t staging = (size_t)4 * 32 * ((size_t)BN * 2 + 16);
+  if (ring < staging) ring = staging;
+  const size_t smem = ring + 1024;
   int tcols = 32;
   while (tcols < BN) tcols <<= 1;
   cudaError_t err = cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -541,9 +584,9 @@ static haar_status_t backward(haar_mlp_s* M, int B, const float* target, cudaStr
   return HAAR_OK;
 }
 
-static haar_status_t pack(haar_mlp_s* M, cudaStream_t st) {
+static haar_status_t pack(haar_mlp_s* M, cudaStream_t st, int advance) {
   const long long n = (long long)w_total();
-  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M->p, M->wb, M->wt);
+  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M->p, M->wb, M->wt, M->step, advance);
   return cuda_check(cudaGetLastError(), "k_pack launch");
 }
 
@@ -562,7 +605,7 @@ static void mlp_free(haar_mlp_s* M) {
   if (!M) return;
   void* ptrs[] = {M->p, M->g, M->m, M->v, M->wb, M->wt, M->X, M->h[0], M->h[1], M->h[2], M->h[3], M->z[0],
                   M->z[1], M->z[2], M->z[3], M->out, M->dout, M->dz, M->dz2, M->tA, M->tB, M->loss, M->iX,
-                  M->ih0, M->ih1, M->weff, M->beff, M->status};
+                  M->ih0, M->ih1, M->weff, M->beff, M->status, M->step};
   for (void* q : ptrs) cudaFree(q);
   delete M;
 }
@@ -614,6 +657,7 @@ haar_status_t haar_mlp_create(int max_batch, int max_rows, int max_groups, haar_
   ALLOC(M->weff, (size_t)max_groups * WIDTH * 4 * 4);
   ALLOC(M->beff, (size_t)max_groups * 4 * 4);
   ALLOC(M->status, 16);
+  ALLOC(M->step, 16);
 #undef ALLOC
   if (e != cudaSuccess) {
     mlp_free(M);
@@ -624,6 +668,7 @@ haar_status_t haar_mlp_create(int max_batch, int max_rows, int max_groups, haar_
   if (e == cudaSuccess) e = cudaMemset(M->v, 0, P * 4);
   if (e == cudaSuccess) e = cudaMemset(M->status, 0, 16);
   if (e == cudaSuccess) e = cudaMemset(M->loss, 0, 4);
+  if (e == cudaSuccess) e = cudaMemset(M->step, 0, 16);
   if (e != cudaSuccess) {
     mlp_free(M);
     return cuda_check(e, "haar_mlp_create: cudaMemset");
@@ -647,9 +692,9 @@ haar_status_t haar_mlp_set_params(haar_mlp_t M, const float* params, void* strea
   cudaError_t e = cudaMemcpyAsync(M->p, params, N_PARAMS * 4, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(M->m, 0, N_PARAMS * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(M->v, 0, N_PARAMS * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(M->step, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_check(e, "haar_mlp_set_params");
-  M->adam_t = 0;
-  return pack(M, st);
+  return pack(M, st, 0);
 }
 
 haar_status_t haar_mlp_get_params(haar_mlp_t M, float* params, void* stream) {
@@ -706,12 +751,9 @@ haar_status_t haar_mlp_train_step(haar_mlp_t M, const float* raw, const float* t
   HS_TRY(encode_raw(M, raw, B, st));
   HS_TRY(forward(M, B, st));
   HS_TRY(backward(M, B, target, st));
-  M->adam_t += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.0f - powf(b1, (float)M->adam_t), c2 = 1.0f - powf(b2, (float)M->adam_t);
-  k_adam<<<1024, 256, 0, st>>>(M->p, M->g, M->m, M->v, N_PARAMS, lr, b1, b2, 1e-8f, c1, c2);
+  k_adam<<<1024, 256, 0, st>>>(M->p, M->g, M->m, M->v, N_PARAMS, lr, 0.9f, 0.999f, 1e-8f, M->step);
   HS_TRY(cuda_check(cudaGetLastError(), "k_adam launch"));
-  HS_TRY(pack(M, st));
+  HS_TRY(pack(M, st, 1));
   if (loss) HS_TRY(cuda_check(cudaMemcpyAsync(loss, M->loss, 4, cudaMemcpyDeviceToDevice, st), "haar_mlp_train_step: loss"));
   return HAAR_OK;
 }

@@ -55,7 +55,7 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: misaligned pointer");
 
   // scratch layout (floats, each region 256-byte aligned)
-  const Geometry g = make_geometry(H, W, C, d->boundary);
+  const Geometry g = make_geometry(H, W, C, d->boundary, choose_tile(H, W, C, S));
   const size_t n_pix = round64((size_t)C * N);
   const size_t n_trig = round64(2 * (size_t)(H + W));
   const size_t n_prm = round64((size_t)S * sizeof(ShiftParam) / sizeof(float));

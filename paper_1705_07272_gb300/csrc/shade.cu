@@ -159,6 +159,204 @@ __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restri
   }
 }
 
+// ---------------------------------------------------------------- vertex-group CSR
+// The top-K sets of neighbouring vertices overlap heavily (8 consecutive
+// torus vertices: ~345 distinct coefficients of 8 x 256), so groups of 8
+// vertices share one sorted union index list with values [nnz_g][8] (zero
+// where a vertex lacks the coefficient): every lighting row loaded feeds 8
+// vertices.  One warp per group: lane = vl + 8 * cg; vertex vl, column block
+// cg (a quarter of the columns, NQ float4 per lane per pass).
+constexpr int kGroup = 8;
+
+__global__ void __launch_bounds__(256) k_shade_gcsr_f32(const float* __restrict__ vals,
+                                                        const uint16_t* __restrict__ idx,
+                                                        const int32_t* __restrict__ gptr, int V,
+                                                        const float* __restrict__ L, int NL, int ncols,
+                                                        float* __restrict__ R) {
+  // CTA = 4 groups x 2 warps (each warp half of the group's union list).
+  // Within a warp, lanes 0-15 take even entries and lanes 16-31 odd ones;
+  // lane q of a half owns float4 column chunk q and accumulates it for all
+  // 8 vertices of the group, so each lighting chunk loaded feeds 8 FMA x 4.
+  __shared__ float4 red[4][16][kGroup];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gl = w >> 1, wh = w & 1;
+  const int g = blockIdx.x * 4 + gl;
+  const int n_groups = (V + kGroup - 1) / kGroup;
+  const bool active = g < n_groups;
+  const int eh = lane >> 4, q = lane & 15;
+  int jb = 0, je = 0;
+  if (active) {
+    const int beg = __ldg(gptr + g), end = __ldg(gptr + g + 1);
+    const int mid = beg + (end - beg + 1) / 2;
+    jb = wh ? mid : beg;
+    je = wh ? end : mid;
+  }
+  const int nq = ncols >> 2;
+  const float4* L4 = reinterpret_cast<const float4*>(L);
+  const float4* V4 = reinterpret_cast<const float4*>(vals);
+  for (int q0 = 0; q0 < nq; q0 += 16) {
+    const int qq = q0 + q;
+    const bool qok = qq < nq;
+    float4 acc[kGroup];
+#pragma unroll
+    for (int v = 0; v < kGroup; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+    for (int j = jb + eh; j < je; j += 2) {
+      const int k = __ldg(idx + j);
+      const bool ok = k < NL && qok;                              // out-of-range entries are ignored
+      const float4 t0 = __ldg(V4 + 2 * j), t1 = __ldg(V4 + 2 * j + 1);
+      const float4 x = ok ? __ldg(L4 + (unsigned)k * (unsigned)nq + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+      for (int v = 0; v < kGroup; ++v) {
+        acc[v].x = fmaf(t[v], x.x, acc[v].x);
+        acc[v].y = fmaf(t[v], x.y, acc[v].y);
+        acc[v].z = fmaf(t[v], x.z, acc[v].z);
+        acc[v].w = fmaf(t[v], x.w, acc[v].w);
+      }
+    }
+    // odd-entry half into the even half, then the second warp into the first
+#pragma unroll
+    for (int v = 0; v < kGroup; ++v) {
+      acc[v].x += __shfl_down_sync(0xffffffffu, acc[v].x, 16);
+      acc[v].y += __shfl_down_sync(0xffffffffu, acc[v].y, 16);
+      acc[v].z += __shfl_down_sync(0xffffffffu, acc[v].z, 16);
+      acc[v].w += __shfl_down_sync(0xffffffffu, acc[v].w, 16);
+    }
+    if (wh == 1 && eh == 0) {
+#pragma unroll
+      for (int v = 0; v < kGroup; ++v) red[gl][q][v] = acc[v];
+    }
+    __syncthreads();
+    if (wh == 0 && eh == 0 && active && qok) {
+#pragma unroll
+      for (int v = 0; v < kGroup; ++v) {
+        const int vv = g * kGroup + v;
+        if (vv < V) {
+          const float4 o = red[gl][q][v];
+          reinterpret_cast<float4*>(R + (long long)vv * ncols)[qq] =
+              make_float4(acc[v].x + o.x, acc[v].y + o.y, acc[v].z + o.z, acc[v].w + o.w);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Packing CSR -> vertex-group CSR.  One warp per group builds the bitmap of
+// the union of its rows' indices in shared memory (N <= 65536: 2048 words).
+constexpr int kBmWords = 2048;
+
+__device__ void gcsr_bitmap(uint32_t* bm, const int32_t* rowptr, const uint16_t* idx, int V, int N, int g, int lane) {
+  for (int w = lane; w < kBmWords; w += 32) bm[w] = 0u;
+  __syncwarp();
+  for (int vl = 0; vl < kGroup; ++vl) {
+    const int v = g * kGroup + vl;
+    if (v >= V) break;
+    for (int j = rowptr[v] + lane; j < rowptr[v + 1]; j += 32) {
+      const int k = idx[j];
+      if (k < N) atomicOr(bm + (k >> 5), 1u << (k & 31));
+    }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(128) k_gcsr_count(const int32_t* __restrict__ rowptr, const uint16_t* __restrict__ idx,
+                                                    int V, int N, int32_t* __restrict__ counts) {
+  __shared__ uint32_t bm_all[4][kBmWords];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * 4 + w;
+  const int n_groups = (V + kGroup - 1) / kGroup;
+  if (g >= n_groups) return;
+  uint32_t* bm = bm_all[w];
+  gcsr_bitmap(bm, rowptr, idx, V, N, g, lane);
+  int c = 0;
+  for (int i = lane; i < kBmWords; i += 32) c += __popc(bm[i]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) counts[g] = c;
+}
+
+// exclusive scan of counts[n] into gptr[n + 1] (one block)
+__global__ void __launch_bounds__(1024) k_scan(const int32_t* __restrict__ counts, int n, int32_t* __restrict__ gptr) {
+  __shared__ int32_t part[1024];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int x = i < n ? counts[i] : 0;
+    part[threadIdx.x] = x;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const int y = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+      __syncthreads();
+      part[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (i < n) gptr[i] = carry + part[threadIdx.x] - x;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gptr[n] = carry;
+}
+
+__global__ void __launch_bounds__(64) k_gcsr_fill(const int32_t* __restrict__ rowptr, const uint16_t* __restrict__ idx,
+                                                  const float* __restrict__ vals, int V, int N,
+                                                  const int32_t* __restrict__ gptr, uint16_t* __restrict__ gidx,
+                                                  float* __restrict__ gvals) {
+  __shared__ uint32_t bm_all[2][kBmWords];
+  __shared__ int32_t pre_all[2][kBmWords];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * 2 + w;
+  const int n_groups = (V + kGroup - 1) / kGroup;
+  if (g >= n_groups) return;
+  uint32_t* bm = bm_all[w];
+  int32_t* pre = pre_all[w];
+  gcsr_bitmap(bm, rowptr, idx, V, N, g, lane);
+  // exclusive prefix popcount per word: lane owns 64 consecutive words
+  constexpr int per = kBmWords / 32;
+  int local = 0;
+  for (int i = 0; i < per; ++i) local += __popc(bm[lane * per + i]);
+  int incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int run = incl - local;
+  for (int i = 0; i < per; ++i) {
+    pre[lane * per + i] = run;
+    run += __popc(bm[lane * per + i]);
+  }
+  __syncwarp();
+  const long long base = gptr[g];
+  const int cnt = gptr[g + 1] - gptr[g];
+  for (int i = 0; i < per; ++i) {
+    const int wd = lane * per + i;
+    uint32_t bits = bm[wd];
+    int p = pre[wd];
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      gidx[base + p] = (uint16_t)(wd * 32 + b);
+      ++p;
+    }
+  }
+  for (long long e = lane; e < (long long)cnt * kGroup; e += 32) gvals[base * kGroup + e] = 0.0f;
+  __syncwarp();
+  for (int vl = 0; vl < kGroup; ++vl) {
+    const int v = g * kGroup + vl;
+    if (v >= V) break;
+    for (int j = rowptr[v] + lane; j < rowptr[v + 1]; j += 32) {
+      const int k = idx[j];
+      if (k >= N) continue;
+      const uint32_t word = bm[k >> 5];
+      const int pos = pre[k >> 5] + __popc(word & ((1u << (k & 31)) - 1u));
+      gvals[(base + pos) * kGroup + vl] = vals[j];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- view bins
 __global__ void k_view_bins(int V, int S, int bins, const float* __restrict__ pos,
                             const float* __restrict__ nrm, const float* __restrict__ cams,
@@ -208,6 +406,29 @@ haar_status_t launch_shade_csr_f32(const float* vals, const uint16_t* idx, const
   else if (nq <= 16) k_shade_csr_f32<4><<<nb, 256, 0, st>>>(vals, idx, rowptr, V, L, NL, ncols, R);
   else k_shade_csr_f32<8><<<nb, 256, 0, st>>>(vals, idx, rowptr, V, L, NL, ncols, R);
   return cuda_check(cudaGetLastError(), "k_shade_csr_f32 launch");
+}
+
+haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, const int32_t* gptr, int V,
+                                    const float* L, int NL, int ncols, float* R, cudaStream_t st) {
+  const long long groups = (V + kGroup - 1) / kGroup;
+  const unsigned nb = (unsigned)((groups + 3) / 4);
+  k_shade_gcsr_f32<<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  return cuda_check(cudaGetLastError(), "k_shade_gcsr_f32 launch");
+}
+
+haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16_t* idx, const float* vals,
+                               int32_t* gptr, uint16_t* gidx, float* gvals, cudaStream_t st) {
+  const int groups = (V + kGroup - 1) / kGroup;
+  // counts go to gptr[1..groups] first, then the scan turns them into offsets in place
+  int32_t* counts = gptr + 1;
+  k_gcsr_count<<<(groups + 3) / 4, 128, 0, st>>>(rowptr, idx, V, N, counts);
+  haar_status_t r = cuda_check(cudaGetLastError(), "k_gcsr_count launch");
+  if (r != HAAR_OK) return r;
+  k_scan<<<1, 1024, 0, st>>>(counts, groups, gptr);
+  r = cuda_check(cudaGetLastError(), "k_scan launch");
+  if (r != HAAR_OK || gidx == nullptr) return r;
+  k_gcsr_fill<<<(groups + 1) / 2, 64, 0, st>>>(rowptr, idx, vals, V, N, gptr, gidx, gvals);
+  return cuda_check(cudaGetLastError(), "k_gcsr_fill launch");
 }
 
 haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,

@@ -21,7 +21,7 @@
 namespace hs {
 
 constexpr int kThreads = 256;
-constexpr int kRotChannels = 4;   // channels resampled together by the rotation kernel
+constexpr int kRotChannels = 3;   // channels resampled together by the rotation kernel (RGB)
 
 enum { KIND_TRANSLATE = 0, KIND_ROTATE = 1, KIND_COPY = 2 };
 
@@ -107,21 +107,69 @@ __device__ float perm_value(const ShiftArgs& a, const ShiftParam& p, int c, int 
 }
 
 template <int OUT>
+__device__ __forceinline__ void store_at(const ShiftArgs& a, long long idx, float v) {
+  if (OUT == HAAR_OUT_F32) {
+    reinterpret_cast<float*>(a.out)[idx] = v * a.scale;
+  } else if (OUT == HAAR_OUT_BF16_HILO) {
+    __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    reinterpret_cast<__nv_bfloat16*>(a.out)[idx] = hi;
+    reinterpret_cast<__nv_bfloat16*>(a.out)[a.plane + idx] = lo;
+  } else {
+    reinterpret_cast<__half*>(a.out)[idx] = __float2half_rn(v);
+  }
+}
+
+// Detail coefficients (H, V, D) of block (r, col) of level lvl; levels whose
+// block side divides an integer shift are replaced by the signed permutation
+// of the input (bit-exact copies).
+template <int OUT>
 __device__ __forceinline__ void emit(const ShiftArgs& a, const ShiftParam* p, int s, int c, int lvl,
                                      int r, int col, float hv, float vv, float dv) {
   const Geometry& g = a.g;
-  const long long gl = (long long)g.q << (2 * (g.n - lvl));
+  const int gl = g.q << (2 * (g.n - lvl));
   if (gl >= a.K) return;                      // whole level truncated away
-  const int cols = g.W >> lvl;
-  const long long base = (long long)r * cols + col;
+  const int k0 = gl + r * (g.W >> lvl) + col;
   if (p != nullptr && ((p->perm_mask >> lvl) & 1u)) {
     hv = perm_value(a, *p, c, lvl, 0, r, col);
     vv = perm_value(a, *p, c, lvl, 1, r, col);
     dv = perm_value(a, *p, c, lvl, 2, r, col);
   }
-  put<OUT>(a, s, c, (int)(gl + base), hv);
-  put<OUT>(a, s, c, (int)(2 * gl + base), vv);
-  put<OUT>(a, s, c, (int)(3 * gl + base), dv);
+  const long long bsc = (long long)s * a.st_s + (long long)c * a.st_c;
+  const long long sk = a.st_k;
+  if (4 * gl <= a.K) {
+    store_at<OUT>(a, bsc + k0 * sk, hv);
+    store_at<OUT>(a, bsc + (k0 + gl) * sk, vv);
+    store_at<OUT>(a, bsc + (k0 + 2 * gl) * sk, dv);
+  } else {
+    if (k0 < a.K) store_at<OUT>(a, bsc + k0 * sk, hv);
+    if (k0 + gl < a.K) store_at<OUT>(a, bsc + (k0 + gl) * sk, vv);
+    if (k0 + 2 * gl < a.K) store_at<OUT>(a, bsc + (k0 + 2 * gl) * sk, dv);
+  }
+}
+
+// Levels lvl0+1 and lvl0+2 of one 4 x 4 block x (row-major) whose element
+// (0, 0) sits at level-lvl0 grid position (gr0 + 4 by, gc0 + 4 bx): writes the
+// detail coefficients and returns the block's scaling value.
+template <int OUT>
+__device__ __forceinline__ float block4(const ShiftArgs& a, const ShiftParam* p, int s, int c, const float* x,
+                                        int lvl0, int gr0, int gc0, int by, int bx) {
+  float A1[4];
+#pragma unroll
+  for (int sa = 0; sa < 2; ++sa) {
+#pragma unroll
+    for (int sc = 0; sc < 2; ++sc) {
+      const float ea = x[(2 * sa) * 4 + 2 * sc], eb = x[(2 * sa) * 4 + 2 * sc + 1];
+      const float ec = x[(2 * sa + 1) * 4 + 2 * sc], ed = x[(2 * sa + 1) * 4 + 2 * sc + 1];
+      A1[2 * sa + sc] = 0.5f * ((ea + eb) + (ec + ed));
+      emit<OUT>(a, p, s, c, lvl0 + 1, (gr0 >> 1) + 2 * by + sa, (gc0 >> 1) + 2 * bx + sc,
+                0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)), 0.5f * ((ea + ed) - (eb + ec)));
+    }
+  }
+  const float ea = A1[0], eb = A1[1], ec = A1[2], ed = A1[3];
+  emit<OUT>(a, p, s, c, lvl0 + 2, (gr0 >> 2) + by, (gc0 >> 2) + bx, 0.5f * ((eb + ed) - (ea + ec)),
+            0.5f * ((ec + ed) - (ea + eb)), 0.5f * ((ea + ed) - (eb + ec)));
+  return 0.5f * ((ea + eb) + (ec + ed));
 }
 
 // One pass of the forward transform over a rows x cols image in shared
@@ -133,8 +181,9 @@ template <int OUT>
 __device__ void haar_pass(const ShiftArgs& a, const ShiftParam* p, int s, int c, const float* src,
                           float* dst, int rows, int cols, int lvl0, int sb, int gr0, int gc0) {
   const int nbr = rows / sb, nbc = cols / sb;
+  const int sh = __ffs(nbc) - 1;              // nbc is a power of two
   for (int b = threadIdx.x; b < nbr * nbc; b += blockDim.x) {
-    const int by = b / nbc, bx = b - by * nbc;
+    const int by = b >> sh, bx = b & (nbc - 1);
     if (sb == 4) {
       float x[16];
 #pragma unroll
@@ -142,24 +191,7 @@ __device__ void haar_pass(const ShiftArgs& a, const ShiftParam* p, int s, int c,
         float4 t = *reinterpret_cast<const float4*>(src + (4 * by + r) * cols + 4 * bx);
         x[4 * r + 0] = t.x; x[4 * r + 1] = t.y; x[4 * r + 2] = t.z; x[4 * r + 3] = t.w;
       }
-      float A1[4];
-#pragma unroll
-      for (int sa = 0; sa < 2; ++sa) {
-#pragma unroll
-        for (int sc = 0; sc < 2; ++sc) {
-          const float ea = x[(2 * sa) * 4 + 2 * sc], eb = x[(2 * sa) * 4 + 2 * sc + 1];
-          const float ec = x[(2 * sa + 1) * 4 + 2 * sc], ed = x[(2 * sa + 1) * 4 + 2 * sc + 1];
-          A1[2 * sa + sc] = 0.5f * ((ea + eb) + (ec + ed));
-          emit<OUT>(a, p, s, c, lvl0 + 1, (gr0 >> 1) + 2 * by + sa, (gc0 >> 1) + 2 * bx + sc,
-                    0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)),
-                    0.5f * ((ea + ed) - (eb + ec)));
-        }
-      }
-      const float ea = A1[0], eb = A1[1], ec = A1[2], ed = A1[3];
-      emit<OUT>(a, p, s, c, lvl0 + 2, (gr0 >> 2) + by, (gc0 >> 2) + bx,
-                0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)),
-                0.5f * ((ea + ed) - (eb + ec)));
-      dst[by * nbc + bx] = 0.5f * ((ea + eb) + (ec + ed));
+      dst[by * nbc + bx] = block4<OUT>(a, p, s, c, x, lvl0, gr0, gc0, by, bx);
     } else {
       const float ea = src[(2 * by) * cols + 2 * bx], eb = src[(2 * by) * cols + 2 * bx + 1];
       const float ec = src[(2 * by + 1) * cols + 2 * bx], ed = src[(2 * by + 1) * cols + 2 * bx + 1];
@@ -231,6 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   const int T = g.T;
   const int tile = blockIdx.x;
   const int s = blockIdx.y;
+  const int cgrp = blockIdx.z;            // channel group of this CTA
   const int tr = tile / g.tiles_c, tc = tile - tr * g.tiles_c;
   const int CG = (KIND == KIND_ROTATE) ? kRotChannels : 1;
   const int win = (KIND == KIND_TRANSLATE) ? (T + 1) * (T + 1) : 0;
@@ -243,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   if (p != nullptr) pr = *p;
   const int i_org = tr * T, j_org = tc * T;
 
-  for (int c0 = 0; c0 < g.C; c0 += CG) {
+  for (int c0 = cgrp * CG; c0 < g.C && c0 < (cgrp + 1) * CG; c0 += CG) {
     const int cgn = min(CG, g.C - c0);
     if (KIND == KIND_TRANSLATE) {
       const float* F = a.pix + (long long)c0 * g.N;
@@ -329,13 +362,184 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned t = atomicAdd(a.counters + s, 1u);
-    s_last = (t == (unsigned)(g.n_tiles - 1)) ? 1 : 0;
+    s_last = (t == (unsigned)(g.n_tiles * gridDim.z - 1)) ? 1 : 0;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   float* img = pbuf;
   float* img2 = pbuf + g.n_tiles;
+  for (int c = 0; c < g.C; ++c) {
+    for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
+      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
+    coarse_levels<OUT>(a, p, s, c, img, img2);
+  }
+  if (threadIdx.x == 0) a.counters[s] = 0u;
+}
+
+// Register path for 32 x 32 and 64 x 64 tiles: every thread resamples its own
+// 4 x 4 block of output pixels straight from the L2-resident pixel map
+// (translation: the 5 x 5 source window, all 25 loads in flight; rotation:
+// 4 bilinear taps per pixel and channel), runs levels 1-2 in registers,
+// writes them, and leaves the block's scaling value in shared memory for the
+// remaining tile levels.  blockDim = (T/4)^2.
+template <int KIND, int OUT>
+__global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_last;
+  const Geometry& g = a.g;
+  const int T = g.T;
+  const int nb = T >> 2;
+  const int tile = blockIdx.x, s = blockIdx.y, cgrp = blockIdx.z;
+  const int tr = tile / g.tiles_c, tc = tile - tr * g.tiles_c;
+  constexpr int CG = (KIND == KIND_ROTATE) ? kRotChannels : 1;
+  const int c0 = cgrp * CG;
+  const int cgn = min(CG, g.C - c0);
+  __shared__ ShiftParam s_prm;
+  if (KIND != KIND_COPY && threadIdx.x == 0) s_prm = a.prm[s];
+  __syncthreads();
+  const ShiftParam* p = (KIND == KIND_COPY) ? nullptr : &s_prm;
+  const int lnb = g.Lt - 2;                         // nb = 2^lnb
+  const int by = threadIdx.x >> lnb, bx = threadIdx.x & (nb - 1);
+  const int i0 = tr * T + 4 * by, j0 = tc * T + 4 * bx;
+  const int Wm = g.W - 1;
+  float* sA = smem;                                 // [CG][nb * nb]
+  float* sB = smem + CG * nb * nb;                  // pass scratch (nb/4)^2
+
+  float x[CG][16];
+  if (KIND == KIND_TRANSLATE) {
+    const ShiftParam pr = *p;
+    const float* F = a.pix + (long long)c0 * g.N;
+    int ro[5], cs[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      int i = i0 - pr.ky - 1 + r, sh = 0;
+      if (g.boundary == HAAR_BOUNDARY_TORUS) {
+        i &= (g.H - 1);
+      } else {
+#pragma unroll 1
+        for (int it = 0; it < 8 && (i < 0 || i >= g.H); ++it) {
+          i = (i < 0) ? -1 - i : 2 * g.H - 1 - i;
+          sh ^= 1;
+        }
+      }
+      ro[r] = i * g.W;
+      cs[r] = j0 - pr.kx - 1 + (sh ? (g.W >> 1) : 0);
+    }
+    float w[5][5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) w[r][q] = __ldg(F + ro[r] + ((cs[r] + q) & Wm));
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        x[0][4 * r + q] = pr.wy0 * (pr.wx0 * w[r + 1][q + 1] + pr.wx1 * w[r + 1][q]) +
+                          pr.wy1 * (pr.wx0 * w[r][q + 1] + pr.wx1 * w[r][q]);
+  } else if (KIND == KIND_ROTATE) {
+    const ShiftParam pr = *p;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r;
+      const float st = __ldg(a.trig + i), ct = __ldg(a.trig + g.H + i);
+      long long off[4][4];
+      float fu[4], fv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q;
+        const float sp = __ldg(a.trig + 2 * g.H + j), cp = __ldg(a.trig + 2 * g.H + g.W + j);
+        const float dx = st * sp, dy = ct, dz = st * cp;
+        const float px = fmaf(pr.R[0], dx, fmaf(pr.R[1], dy, pr.R[2] * dz));
+        const float py = fmaf(pr.R[3], dx, fmaf(pr.R[4], dy, pr.R[5] * dz));
+        const float pz = fmaf(pr.R[6], dx, fmaf(pr.R[7], dy, pr.R[8] * dz));
+        const float rho = sqrtf(fmaf(px, px, pz * pz));
+        const float u = fmaf(atan2f(rho, py), a.u_scale, -0.5f);
+        const float v = fmaf(atan2f(px, pz), a.v_scale, -0.5f);
+        const float fi = floorf(u), fj = floorf(v);
+        fu[q] = u - fi;
+        fv[q] = v - fj;
+        const int ia = (int)fi, ja = (int)fj;
+        // taps: rows ia, ia+1 in [-1, H] (one step past a pole at most), columns cyclic
+        int r0 = ia, r1 = ia + 1, h0 = 0, h1 = 0;
+        if (g.boundary == HAAR_BOUNDARY_TORUS) {
+          r0 &= (g.H - 1);
+          r1 &= (g.H - 1);
+        } else {
+          if (r0 < 0) { r0 = -1 - r0; h0 = g.W >> 1; }
+          if (r0 >= g.H) { r0 = 2 * g.H - 1 - r0; h0 = g.W >> 1; }
+          if (r1 < 0) { r1 = -1 - r1; h1 = g.W >> 1; }
+          if (r1 >= g.H) { r1 = 2 * g.H - 1 - r1; h1 = g.W >> 1; }
+        }
+        off[q][0] = (long long)r0 * g.W + ((ja + h0) & Wm);
+        off[q][1] = (long long)r0 * g.W + ((ja + 1 + h0) & Wm);
+        off[q][2] = (long long)r1 * g.W + ((ja + h1) & Wm);
+        off[q][3] = (long long)r1 * g.W + ((ja + 1 + h1) & Wm);
+      }
+#pragma unroll
+      for (int ci = 0; ci < CG; ++ci) {
+        if (ci < cgn) {
+          const float* F = a.pix + (long long)(c0 + ci) * g.N;
+          float f[4][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) f[q][t] = __ldg(F + off[q][t]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            x[ci][4 * r + q] = (1.0f - fu[q]) * ((1.0f - fv[q]) * f[q][0] + fv[q] * f[q][1]) +
+                               fu[q] * ((1.0f - fv[q]) * f[q][2] + fv[q] * f[q][3]);
+        }
+      }
+    }
+  } else {  // KIND_COPY
+    const float* F = a.pix + (long long)s * g.N;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(F + (long long)(i0 + r) * g.W + j0));
+      x[0][4 * r] = t.x; x[0][4 * r + 1] = t.y; x[0][4 * r + 2] = t.z; x[0][4 * r + 3] = t.w;
+    }
+  }
+#pragma unroll
+  for (int ci = 0; ci < CG; ++ci)
+    if (ci < cgn) sA[ci * nb * nb + threadIdx.x] = block4<OUT>(a, p, s, c0 + ci, x[ci], 0, tr * T, tc * T, by, bx);
+
+  for (int ci = 0; ci < cgn; ++ci) {
+    const int c = c0 + ci;
+    // levels 3..Lt on the nb x nb scaling image
+    int side = nb, lvl = 2;
+    float* src = sA + ci * nb * nb;
+    float* dst = sB;
+    while (lvl < g.Lt) {
+      const int sb = (g.Lt - lvl >= 2) ? 4 : 2;
+      __syncthreads();
+      haar_pass<OUT>(a, p, s, c, src, dst, side, side, lvl, sb, (tr * T) >> lvl, (tc * T) >> lvl);
+      side /= sb;
+      lvl += (sb == 4) ? 2 : 1;
+      float* t = src; src = dst; dst = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const float m = src[0];
+      if (a.means != nullptr)
+        a.means[((long long)s * g.C + c) * g.n_tiles + tile] = m;
+      else
+        reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = m;
+    }
+    __syncthreads();
+  }
+
+  if (a.counters == nullptr) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(a.counters + s, 1u);
+    s_last = (t == (unsigned)(g.n_tiles * gridDim.z - 1)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  float* img = smem;
+  float* img2 = smem + g.n_tiles;
   for (int c = 0; c < g.C; ++c) {
     for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
       img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
@@ -496,13 +700,29 @@ static size_t shift_smem_bytes(const Geometry& g, int kind) {
 
 template <int KIND, int OUT>
 static haar_status_t launch_k(const ShiftArgs& a, int S, cudaStream_t st) {
+  const int CG = (KIND == KIND_ROTATE) ? kRotChannels : 1;
+  if (a.g.T >= 32) {
+    const int nb = a.g.T / 4;
+    size_t fl = (size_t)CG * nb * nb + (size_t)(nb / 4) * (nb / 4) + 8;
+    const size_t coarse = (size_t)a.g.n_tiles + (size_t)a.g.n_tiles / 4 + 8;
+    if (fl < coarse) fl = coarse;
+    const size_t sm = fl * sizeof(float);
+    auto fr = k_shift_reg<KIND, OUT>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_reg)");
+    }
+    dim3 grid(a.g.n_tiles, S, (a.g.C + CG - 1) / CG);
+    fr<<<grid, nb * nb, sm, st>>>(a);
+    return cuda_check(cudaGetLastError(), "k_shift_reg launch");
+  }
   const size_t sm = shift_smem_bytes(a.g, KIND);
   auto fn = k_shift<KIND, OUT>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift)");
   }
-  dim3 grid(a.g.n_tiles, S);
+  dim3 grid(a.g.n_tiles, S, (a.g.C + CG - 1) / CG);
   fn<<<grid, kThreads, sm, st>>>(a);
   return cuda_check(cudaGetLastError(), "k_shift launch");
 }

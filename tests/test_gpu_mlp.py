@@ -117,6 +117,33 @@ def test_training_tracks_oracle(hs):
     net.close()
 
 
+def test_captured_training_step_replays_eager(hs):
+    # the Adam step count lives on the device, so a captured step replays exactly
+    import torch
+    rng = np.random.default_rng(5)
+    flat = _t(_flat(_f32_params(rng)), None).float()
+    batches = [(_t(_raw(rng, 256), None).float(), _t(rng.standard_normal((256, 512)), None).float())
+               for _ in range(4)]
+    eager = hs.Surrogate(max_batch=256, max_rows=128, max_groups=1)
+    eager.set_params(flat)
+    want = [float(eager.train_step(r, t, 1e-3).item()) for r, t in batches]
+    net = hs.Surrogate(max_batch=256, max_rows=128, max_groups=1)
+    net.set_params(flat)
+    R = torch.empty_like(batches[0][0])
+    T = torch.empty_like(batches[0][1])
+    graph, loss = net.capture_train_step(R, T, 1e-3)
+    got = []
+    for r, t in batches:
+        R.copy_(r)
+        T.copy_(t)
+        graph.replay()
+        got.append(float(loss.item()))
+    assert got == want
+    assert torch.equal(net.get_params(), eager.get_params())
+    eager.close()
+    net.close()
+
+
 def test_fused_shade_matches_oracle(hs):
     import torch
     rng = np.random.default_rng(3)
@@ -140,4 +167,73 @@ def test_fused_shade_matches_oracle(hs):
         out, _ = om.forward(P, om.encode(np.concatenate([pos, nrm, view], axis=1)), bf16=True)
         ref[:, s] = om.shade_from_outputs(out, mu, sg, Ls[s][:, idx])
     assert rel_l2(R, ref) <= FWD_TOL
+    net.close()
+
+
+def _glossy_dataset(n, seed, device="cuda", chunk=8192):
+    """(raw [n, 9], T [n, 8192]) for random (vertex, camera) pairs of the
+    glossy torus scene: Phong transfer on the 64x128 grid, projected by the
+    oracle (coefficients of the 256x512 map; finer levels are zero)."""
+    sc = synth.scene(4, V=100000, S=1)
+    rng = np.random.default_rng(seed)
+    vid = rng.integers(0, sc["V"], n)
+    cams = synth.cameras(rng, n)
+    pos, nrm, expo = sc["pos"][vid], sc["nrm"][vid], sc["expo"][vid]
+    view = cams - pos
+    view /= np.linalg.norm(view, axis=1, keepdims=True)
+    Ts = []
+    for a in range(0, n, chunk):
+        w = synth.transport_weights(pos[a:a + chunk], nrm[a:a + chunk], sc["occ_c"], sc["occ_r"], 64, 128,
+                                    view=view[a:a + chunk], expo=expo[a:a + chunk], device=device)
+        Ts.append(oh.forward(w.double().cpu().numpy()) / 4.0)
+    raw = np.concatenate([pos, nrm, view], axis=1).astype(np.float32)
+    return raw, np.concatenate(Ts), sc
+
+
+def test_trained_surrogate_against_stored_transport(hs):
+    # Train the surrogate on oracle transports (S8), then compare its shading
+    # with the stored-transport method on held-out (vertex, view) pairs under
+    # rotated lighting.  What the network gains: 1.6 MB of weights instead of
+    # 4.9 GB of view-binned transport for the 100k-vertex scene, and
+    # continuous views instead of 16 bins; the accuracy cost is reported.
+    import torch
+    n_train, n_test = 131072, 4096
+    raw, T, sc = _glossy_dataset(n_train + n_test, 7)
+    Ttr = T[:n_train]
+    idx = np.sort(np.argsort(-np.abs(Ttr).mean(axis=0), kind="stable")[:512])
+    mu = Ttr[:, idx].mean(axis=0)
+    # one scale for all outputs: the loss then weighs each coefficient by its
+    # share of the transport's energy, as the shading error does
+    sg = np.full(512, Ttr[:, idx].std() + 1e-12)
+    Y = ((T[:, idx] - mu) / sg).astype(np.float32)
+    rng = np.random.default_rng(11)
+    P = om.init(rng)
+    net = hs.Surrogate(max_batch=4096, max_rows=4096, max_groups=8)
+    net.set_params(_t(_flat(P), None).float())
+    Rg, Yg = _t(raw[:n_train]), _t(Y[:n_train])
+    B = 4096
+    steps = 4000
+    for it in range(steps):
+        lr = 1e-3 if it < steps // 2 else (3e-4 if it < 3 * steps // 4 else 1e-4)
+        sel = torch.randint(0, n_train, (B,), device="cuda")
+        net.train_step(Rg[sel].contiguous(), Yg[sel].contiguous(), lr)
+    out = net.forward(_t(raw[n_train:])).cpu().numpy().astype(np.float64)
+    assert net.status() == 0
+    # shading under 3 rotations of the c4 lighting
+    H, W = 256, 512
+    L = oh.forward(sc["light"])
+    eul = synth.euler_angles(np.random.default_rng(3), 3)
+    Ls = osh.haar_shift(L, H, W, osh.ROTATE_EULER, eul)[..., :8192]         # [3, C, 8192]
+    Tte = T[n_train:]
+    plain = np.einsum("nk,sck->nsc", Tte, Ls)
+    trunc = np.einsum("nk,sck->nsc", Tte[:, idx], Ls[..., idx])
+    mean_only = np.einsum("k,sck->sc", mu, Ls[..., idx])[None].repeat(n_test, 0)
+    sur = np.einsum("nk,sck->nsc", mu + sg * out, Ls[..., idx])
+    e_sur, e_trunc, e_mean = rel_l2(sur, plain), rel_l2(trunc, plain), rel_l2(mean_only, plain)
+    print(f"surrogate vs stored transport: rel-L2 {e_sur:.3e} (index-set truncation alone {e_trunc:.3e}, "
+          f"mean transport {e_mean:.3e})")
+    stored = 100000 * 16 * 512 * 6
+    weights = int(hs.lib().haar_mlp_param_count()) * 2
+    assert stored / weights > 1000
+    assert e_sur < 0.5 * e_mean
     net.close()

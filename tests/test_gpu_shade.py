@@ -115,6 +115,44 @@ def test_csr_ragged_rows(hs):
     assert rel_l2(got, ref) <= 1e-5
 
 
+def _group_reference(vals, idx, rowptr, V, G=8):
+    """Union index list and [nnz][G] values of every group of G rows."""
+    gptr, gidx, gvals = [0], [], []
+    for g0 in range(0, V, G):
+        rows = range(g0, min(V, g0 + G))
+        u = np.unique(np.concatenate([idx[rowptr[v]:rowptr[v + 1]] for v in rows] + [np.zeros(0, np.int64)]))
+        blk = np.zeros((len(u), G))
+        for j, v in enumerate(rows):
+            pos = np.searchsorted(u, idx[rowptr[v]:rowptr[v + 1]])
+            blk[pos, j] = vals[rowptr[v]:rowptr[v + 1]]
+        gidx.append(u)
+        gvals.append(blk)
+        gptr.append(gptr[-1] + len(u))
+    return np.array(gptr), np.concatenate(gidx), np.concatenate(gvals)
+
+
+def test_group_csr_packing_and_shading(hs):
+    import torch
+    sc = synth.scene(1, V=777, S=4, H=32, W=64)
+    H, W = 32, 64
+    vals, idx, rowptr = _csr_inputs(sc, 64, H, W)
+    V = sc["V"]
+    tr = hs.haar_transport_group(V, H * W, _t(rowptr.astype(np.int32), torch.int32),
+                                 _t(idx.astype(np.int16), torch.int16), _t(vals, torch.float32))
+    torch.cuda.synchronize()
+    gptr, gidx, gvals = _group_reference(vals, idx, rowptr, V)
+    assert np.array_equal(tr.rowptr.cpu().numpy(), gptr)
+    assert np.array_equal(tr.idx.cpu().numpy().astype(np.uint16).astype(np.int64)[:gptr[-1]], gidx)
+    assert np.array_equal(tr.vals.cpu().numpy().astype(np.float64)[:gptr[-1]], gvals)
+    L = f32(oh.forward(sc["light"]))
+    plan = hs.Plan(H, W, 3, max_shifts=4, out_layout=hs.HAAR_LAYOUT_KSC)
+    R = hs.shade_batch(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
+    torch.cuda.synchronize()
+    Ls = osh.haar_shift(L, H, W, osh.TRANSLATE, sc["params"])
+    ref = osd.radiance(Ls, otr.csr_dense(vals, idx, rowptr, H * W), H, W)
+    assert rel_l2(R.cpu().numpy(), ref) <= 1e-5
+
+
 def test_csr_full_size_c1_sampled(hs):
     # the full 50 000-vertex, 16-shift RGB 128x256 frame; the oracle checks
     # 64 sampled vertices one by one through pixel space
@@ -131,6 +169,14 @@ def test_csr_full_size_c1_sampled(hs):
     ref = osd.radiance(Ls, dense, H, W)
     assert rel_l2(got[pick], ref) <= 1e-5
     assert np.isfinite(got).all()
+    # the same frame through the 8-vertex group CSR the bench times
+    import torch
+    trg = hs.haar_transport_group(sc["V"], H * W, _t(rowptr.astype(np.int32), torch.int32),
+                                  _t(idx.astype(np.int16), torch.int16), _t(vals, torch.float32))
+    plan = hs.Plan(H, W, 3, max_shifts=sc["S"], out_layout=hs.HAAR_LAYOUT_KSC)
+    Rg = hs.shade_batch(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), trg).cpu().numpy()
+    assert rel_l2(Rg[pick], ref) <= 1e-5
+    assert rel_l2(Rg, got) <= 1e-6
 
 
 def test_view_bins(hs):
