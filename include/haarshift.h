@@ -234,7 +234,7 @@ HAAR_API haar_status_t haar_view_bins(int V, int S, int bins, const float* pos, 
 
 /* ---------------------------------------------------------------------------
  * Transport surrogate (not in the paper; a learned stand-in for stored
- * transport).  A 4 x 256 GELU MLP maps a vertex's position, normal and view
+ * transport).  A 4 x 256 GELU MLP (tanh-form GELU) maps a vertex's position, normal and view
  * direction to its transport coefficients at a fixed set of 512 canonical
  * indices (standardised: T_j = mu_j + sigma_j out_j).  Encoding of the 9
  * inputs: x, sin(w_f x), cos(w_f x) with w_f = pi 2^(f/2), f = 0..15, zero-padded

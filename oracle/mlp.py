@@ -7,7 +7,8 @@ transport coefficients at a fixed index set:
 * encoding: the 9 inputs, then sin and cos of omega_f * input for 16
   frequencies omega_f = pi * 2^(f/2), f = 0..15 (297 features), zero-padded
   to 320;
-* 4 hidden layers of width 256 with GELU, gelu(z) = z (1 + erf(z / sqrt 2)) / 2;
+* 4 hidden layers of width 256 with GELU in its tanh form (Hendrycks and
+  Gimpel 2016): gelu(z) = z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) / 2;
 * a linear output layer of width 512 (standardised coefficients);
 * loss: mean squared error over batch and outputs.
 
@@ -22,7 +23,6 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import erf
 
 from .transport import to_bf16
 
@@ -53,12 +53,17 @@ def encode(raw: np.ndarray) -> np.ndarray:
     return out
 
 
+GELU_A = math.sqrt(2.0 / math.pi)
+GELU_B = 0.044715
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(GELU_A * (z + GELU_B * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    t = np.tanh(GELU_A * (z + GELU_B * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_A * (1.0 + 3.0 * GELU_B * z * z)
 
 
 def init(rng: np.random.Generator):

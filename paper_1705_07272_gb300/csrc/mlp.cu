@@ -6,7 +6,7 @@
 // the shifted lighting directly (the output layer folded into the lighting).
 //
 // Encoding (9 inputs): x, then sin(w_f x), cos(w_f x) for w_f = pi 2^(f/2),
-// f = 0..15 (297 features, zero-padded to 320).  Flat parameter layout:
+// f = 0..15 (297 features, zero-padded to 320).  GELU in its tanh form.  Flat parameter layout:
 // W1[256][320] b1[256] W2[256][256] b2 W3 b3 W4 b4 Wo[512][256] bo[512].
 #include <math.h>
 #include <string.h>
@@ -49,9 +49,23 @@ struct EpiArgs {
   float* radiance;         // EPI_SHADE: R[v][s][c], row m + row0 = s * rows_per_group + v
 };
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU in its tanh form (Hendrycks and Gimpel 2016), with the hardware tanh
+// approximation (tanh.approx.f32, relative error ~2^-11, below the bf16
+// rounding of the stored activations).
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kGeluA = 0.79788456080286536f;   // sqrt(2 / pi)
+constexpr float kGeluB = 0.044715f;
+__device__ __forceinline__ float gelu(float z) {
+  const float t = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
+  return 0.5f * z * (1.0f + t);
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+  const float t = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * kGeluA * fmaf(3.0f * kGeluB, z * z, 1.0f);
 }
 
 struct __align__(8) GBars {
@@ -250,19 +264,18 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
 
 // -------------------------------------------------------------- helper kernels
 
-__device__ __forceinline__ void encode_row(const float raw[N_RAW], __nv_bfloat16* out, int j0, int jstep) {
-  for (int j = j0; j < N_IN; j += jstep) {
-    float x = 0.0f;
-    if (j < N_RAW) {
-      x = raw[j];
-    } else if (j < N_RAW + 2 * N_FREQ * N_RAW) {
-      const int t = j - N_RAW;
-      const int f = t / (2 * N_RAW), r = t - f * 2 * N_RAW;
-      const float w = 3.14159265358979323846f * exp2f(0.5f * (float)f);
-      x = (r < N_RAW) ? sinf(w * raw[r]) : cosf(w * raw[r - N_RAW]);
-    }
-    out[j] = __float2bfloat16_rn(x);
+__device__ __forceinline__ void encode_row(const float raw[N_RAW], __nv_bfloat16* out, int lane) {
+  // lanes 0..143 (in steps of 32) take one (frequency, input) pair: sin and cos together
+  for (int t = lane; t < N_FREQ * N_RAW; t += 32) {
+    const int f = t / N_RAW, r = t - f * N_RAW;
+    const float w = 3.14159265358979323846f * exp2f(0.5f * (float)f);
+    float sv, cv;
+    sincosf(w * raw[r], &sv, &cv);
+    out[N_RAW + 2 * N_RAW * f + r] = __float2bfloat16_rn(sv);
+    out[N_RAW + 2 * N_RAW * f + N_RAW + r] = __float2bfloat16_rn(cv);
   }
+  if (lane < N_RAW) out[lane] = __float2bfloat16_rn(raw[lane]);
+  for (int j = N_RAW + 2 * N_FREQ * N_RAW + lane; j < N_IN; j += 32) out[j] = __float2bfloat16_rn(0.0f);
 }
 
 // X[b][320] from raw inputs [b][9]
@@ -271,7 +284,7 @@ __global__ void k_encode_raw(const float* __restrict__ raw, int B, __nv_bfloat16
   if (b >= B) return;
   float r[N_RAW];
   for (int i = 0; i < N_RAW; ++i) r[i] = raw[(long long)b * N_RAW + i];
-  encode_row(r, X + (long long)b * N_IN, threadIdx.x & 31, 32);
+  encode_row(r, X + (long long)b * N_IN, threadIdx.x & 31);
 }
 
 // X[row][320] for rows row0.. of the (s, v) grid, row = s * V + v:
@@ -291,7 +304,7 @@ __global__ void k_encode_scene(const float* __restrict__ pos, const float* __res
   float wx = cams[3 * s] - raw[0], wy = cams[3 * s + 1] - raw[1], wz = cams[3 * s + 2] - raw[2];
   const float inv = rsqrtf(wx * wx + wy * wy + wz * wz);
   raw[6] = wx * inv; raw[7] = wy * inv; raw[8] = wz * inv;
-  encode_row(raw, X + (long long)r * N_IN, threadIdx.x & 31, 32);
+  encode_row(raw, X + (long long)r * N_IN, threadIdx.x & 31);
 }
 
 // out[c][r] = in[r][c] (bf16), 32 x 32 tiles

@@ -119,43 +119,75 @@ __global__ void __launch_bounds__(256) k_shade_csr_f32(const float* __restrict__
 }
 
 // ---------------------------------------------------------------- bin-CSR FP16
-// One warp per (vertex, s), vertex-major so the bins of one vertex are reused
-// across its shifts from L1/L2.  Lighting layout L[s][k][c] (channels
-// interleaved), NL coefficients per (s, c).
+// A CTA takes 16 vertices and walks the shifts s in order, so all its warps
+// gather from the same shifted lighting L[s] (L1-resident: the top-K indices
+// of a vertex stay within the coarse levels) while the 16 vertices' bin rows
+// stay in L2 across shifts.  Each lane reads 16 consecutive entries of a bin
+// row with vector loads (2 x 16 B of halves, 4 x 16 B of indices).
+// Lighting layout L[s][k][c] (channels interleaved), NL coefficients per (s, c).
+constexpr int kBinVerts = 16;
+
 __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restrict__ vals,
                                                           const uint32_t* __restrict__ idx,
                                                           const uint8_t* __restrict__ bin_of, int V,
                                                           int bins, int K, int S, int C,
                                                           const float* __restrict__ L, long long NL,
                                                           float* __restrict__ R) {
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= (long long)V * S) return;
-  const int v = (int)(warp / S), s = (int)(warp - (long long)v * S);
-  const int b = __ldg(bin_of + (long long)s * V + v);
-  const long long row = ((long long)v * bins + b) * K;
-  const float* Ls = L + (long long)s * NL * C;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-  for (int j = lane; j < K; j += 32) {
-    const long long k0 = __ldg(idx + row + j);
-    const bool ok = k0 < NL;                                // out-of-range entries are ignored
-    const float t = ok ? __half2float(vals[row + j]) : 0.0f;
-    const float* lk = Ls + (ok ? k0 : 0) * C;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v0 = blockIdx.x * kBinVerts;
+  const bool vec = (K % 512) == 0;                      // 16 entries per lane per 512-entry slab
+  for (int s = 0; s < S; ++s) {
+    const float* Ls = L + (long long)s * NL * C;
+    for (int vi = w; vi < kBinVerts; vi += 8) {
+      const int v = v0 + vi;
+      if (v >= V) break;
+      const int b = __ldg(bin_of + (long long)s * V + v);
+      const long long row = ((long long)v * bins + b) * K;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      if (vec) {
+        for (int j0 = 16 * lane; j0 < K; j0 += 512) {
+          const uint4 h0 = __ldg(reinterpret_cast<const uint4*>(vals + row + j0));
+          const uint4 h1 = __ldg(reinterpret_cast<const uint4*>(vals + row + j0 + 8));
+          uint4 ix[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
-  }
+          for (int i = 0; i < 4; ++i) ix[i] = __ldg(reinterpret_cast<const uint4*>(idx + row + j0 + 4 * i));
+          const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+          const uint32_t kw[16] = {ix[0].x, ix[0].y, ix[0].z, ix[0].w, ix[1].x, ix[1].y, ix[1].z, ix[1].w,
+                                   ix[2].x, ix[2].y, ix[2].z, ix[2].w, ix[3].x, ix[3].y, ix[3].z, ix[3].w};
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    float x = acc[c];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    acc[c] = x;
-  }
-  if (lane == 0) {
+          for (int e = 0; e < 16; ++e) {
+            const uint32_t bits = (e & 1) ? (hw[e >> 1] >> 16) : (hw[e >> 1] & 0xFFFFu);
+            const bool ok = kw[e] < (uint32_t)NL;               // out-of-range entries are ignored
+            const float t = ok ? __half2float(__ushort_as_half((unsigned short)bits)) : 0.0f;
+            const float* lk = Ls + (long long)(ok ? kw[e] : 0u) * C;
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (c < C) R[((long long)v * S + s) * C + c] = acc[c];
+            for (int c = 0; c < 4; ++c)
+              if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
+          }
+        }
+      } else {
+        for (int j = lane; j < K; j += 32) {
+          const long long k0 = __ldg(idx + row + j);
+          const bool ok = k0 < NL;
+          const float t = ok ? __half2float(vals[row + j]) : 0.0f;
+          const float* lk = Ls + (ok ? k0 : 0) * C;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float x = acc[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        acc[c] = x;
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < C) R[((long long)v * S + s) * C + c] = acc[c];
+      }
+    }
   }
 }
 
@@ -168,16 +200,21 @@ __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restri
 // cg (a quarter of the columns, NQ float4 per lane per pass).
 constexpr int kGroup = 8;
 
-__global__ void __launch_bounds__(256) k_shade_gcsr_f32(const float* __restrict__ vals,
-                                                        const uint16_t* __restrict__ idx,
-                                                        const int32_t* __restrict__ gptr, int V,
-                                                        const float* __restrict__ L, int NL, int ncols,
-                                                        float* __restrict__ R) {
+__global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restrict__ vals,
+                                                           const uint16_t* __restrict__ idx,
+                                                           const int32_t* __restrict__ gptr, int V,
+                                                           const float* __restrict__ L, int NL, int ncols,
+                                                           float* __restrict__ R) {
   // CTA = 4 groups x 2 warps (each warp half of the group's union list).
-  // Within a warp, lanes 0-15 take even entries and lanes 16-31 odd ones;
-  // lane q of a half owns float4 column chunk q and accumulates it for all
-  // 8 vertices of the group, so each lighting chunk loaded feeds 8 FMA x 4.
+  // The union list is streamed in batches of 32 entries: one coalesced load
+  // of 32 indices (kept in a register, broadcast by shuffles) and of their
+  // 32 x 8 values (staged in shared memory), the next batch prefetched into
+  // registers while the current one is consumed.  Lanes 0-15 take even
+  // entries, lanes 16-31 odd ones; lane q of a half owns float4 column chunk
+  // q for all 8 vertices of the group, so each lighting chunk loaded feeds
+  // 32 FMAs.
   __shared__ float4 red[4][16][kGroup];
+  __shared__ float4 sv[8][32][2];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gl = w >> 1, wh = w & 1;
   const int g = blockIdx.x * 4 + gl;
@@ -200,19 +237,44 @@ __global__ void __launch_bounds__(256) k_shade_gcsr_f32(const float* __restrict_
     float4 acc[kGroup];
 #pragma unroll
     for (int v = 0; v < kGroup; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 2
-    for (int j = jb + eh; j < je; j += 2) {
-      const int k = __ldg(idx + j);
-      const bool ok = k < NL && qok;                              // out-of-range entries are ignored
-      const float4 t0 = __ldg(V4 + 2 * j), t1 = __ldg(V4 + 2 * j + 1);
-      const float4 x = ok ? __ldg(L4 + (unsigned)k * (unsigned)nq + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+    // prefetch the first batch
+    int nk = NL;
+    float4 nv0 = make_float4(0.f, 0.f, 0.f, 0.f), nv1 = nv0;
+    if (jb + lane < je) {
+      nk = __ldg(idx + jb + lane);
+      nv0 = __ldg(V4 + 2 * (jb + lane));
+      nv1 = __ldg(V4 + 2 * (jb + lane) + 1);
+    }
+    for (int j0 = jb; j0 < je; j0 += 32) {
+      const int cnt = min(32, je - j0);
+      const int myk = nk;
+      __syncwarp();
+      sv[w][lane][0] = nv0;
+      sv[w][lane][1] = nv1;
+      __syncwarp();
+      const int jn = j0 + 32 + lane;
+      nk = NL;
+      if (jn < je) {
+        nk = __ldg(idx + jn);
+        nv0 = __ldg(V4 + 2 * jn);
+        nv1 = __ldg(V4 + 2 * jn + 1);
+      }
+      const int pairs = (cnt + 1) >> 1;                            // same trip count in both halves
+#pragma unroll 4
+      for (int pp = 0; pp < pairs; ++pp) {
+        const int e = 2 * pp + eh;
+        const int k = __shfl_sync(0xffffffffu, myk, e & 31);
+        const bool ok = e < cnt && k < NL && qok;                  // out-of-range entries are ignored
+        const float4 x = ok ? __ldg(L4 + (unsigned)k * (unsigned)nq + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 t0 = sv[w][e & 31][0], t1 = sv[w][e & 31][1];
+        const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
-      for (int v = 0; v < kGroup; ++v) {
-        acc[v].x = fmaf(t[v], x.x, acc[v].x);
-        acc[v].y = fmaf(t[v], x.y, acc[v].y);
-        acc[v].z = fmaf(t[v], x.z, acc[v].z);
-        acc[v].w = fmaf(t[v], x.w, acc[v].w);
+        for (int v = 0; v < kGroup; ++v) {
+          acc[v].x = fmaf(t[v], x.x, acc[v].x);
+          acc[v].y = fmaf(t[v], x.y, acc[v].y);
+          acc[v].z = fmaf(t[v], x.z, acc[v].z);
+          acc[v].w = fmaf(t[v], x.w, acc[v].w);
+        }
       }
     }
     // odd-entry half into the even half, then the second warp into the first
@@ -434,9 +496,8 @@ haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16
 haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,
                                       int V, int bins, int K, int S, int C, const float* L, long long NL,
                                       float* R, cudaStream_t st) {
-  const long long threads = (long long)V * S * 32;
-  k_shade_bincsr_f16<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(vals, idx, bin_of, V, bins, K, S,
-                                                                        C, L, NL, R);
+  const unsigned nb = (unsigned)((V + kBinVerts - 1) / kBinVerts);
+  k_shade_bincsr_f16<<<nb, 256, 0, st>>>(vals, idx, bin_of, V, bins, K, S, C, L, NL, R);
   return cuda_check(cudaGetLastError(), "k_shade_bincsr_f16 launch");
 }
 

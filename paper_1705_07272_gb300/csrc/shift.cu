@@ -500,9 +500,50 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
       x[0][4 * r] = t.x; x[0][4 * r + 1] = t.y; x[0][4 * r + 2] = t.z; x[0][4 * r + 3] = t.w;
     }
   }
+  // Fast store path (float32, coefficients contiguous in k, no permuted
+  // level, levels 1-2 kept whole): the thread's level-1 coefficients are
+  // three 2 x 2 patches (one per band) written as float2 pairs.
+  const int g1 = g.q << (2 * (g.n - 1)), g2 = g.q << (2 * (g.n - 2));
+  const bool fast = OUT == HAAR_OUT_F32 && a.st_k == 1 && a.scale == 1.0f && (p == nullptr || p->perm_mask == 0u) &&
+                    4 * g1 <= a.K && g.n >= 2;
 #pragma unroll
-  for (int ci = 0; ci < CG; ++ci)
-    if (ci < cgn) sA[ci * nb * nb + threadIdx.x] = block4<OUT>(a, p, s, c0 + ci, x[ci], 0, tr * T, tc * T, by, bx);
+  for (int ci = 0; ci < CG; ++ci) {
+    if (ci >= cgn) continue;
+    if (fast) {
+      float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)(c0 + ci) * a.st_c;
+      const float* xb = x[ci];
+      float A1[4], D1[3][4];
+#pragma unroll
+      for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+        for (int sc = 0; sc < 2; ++sc) {
+          const float ea = xb[(2 * sa) * 4 + 2 * sc], eb = xb[(2 * sa) * 4 + 2 * sc + 1];
+          const float ec = xb[(2 * sa + 1) * 4 + 2 * sc], ed = xb[(2 * sa + 1) * 4 + 2 * sc + 1];
+          A1[2 * sa + sc] = 0.5f * ((ea + eb) + (ec + ed));
+          D1[0][2 * sa + sc] = 0.5f * ((eb + ed) - (ea + ec));
+          D1[1][2 * sa + sc] = 0.5f * ((ec + ed) - (ea + eb));
+          D1[2][2 * sa + sc] = 0.5f * ((ea + ed) - (eb + ec));
+        }
+      const int cols1 = g.W >> 1, cols2 = g.W >> 2;
+      const int r1 = ((tr * T) >> 1) + 2 * by, c1 = ((tc * T) >> 1) + 2 * bx;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        float* pb = ob + (long long)g1 * (1 + b) + (long long)r1 * cols1 + c1;
+        *reinterpret_cast<float2*>(pb) = make_float2(D1[b][0], D1[b][1]);
+        *reinterpret_cast<float2*>(pb + cols1) = make_float2(D1[b][2], D1[b][3]);
+      }
+      const float ea = A1[0], eb = A1[1], ec = A1[2], ed = A1[3];
+      if (4 * g2 <= a.K) {
+        float* p2 = ob + ((long long)((tr * T) >> 2) + by) * cols2 + ((tc * T) >> 2) + bx;
+        p2[g2] = 0.5f * ((eb + ed) - (ea + ec));
+        p2[2 * g2] = 0.5f * ((ec + ed) - (ea + eb));
+        p2[3 * g2] = 0.5f * ((ea + ed) - (eb + ec));
+      }
+      sA[ci * nb * nb + threadIdx.x] = 0.5f * ((ea + eb) + (ec + ed));
+    } else {
+      sA[ci * nb * nb + threadIdx.x] = block4<OUT>(a, p, s, c0 + ci, x[ci], 0, tr * T, tc * T, by, bx);
+    }
+  }
 
   for (int ci = 0; ci < cgn; ++ci) {
     const int c = c0 + ci;

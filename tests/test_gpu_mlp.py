@@ -138,7 +138,8 @@ def test_captured_training_step_replays_eager(hs):
         T.copy_(t)
         graph.replay()
         got.append(float(loss.item()))
-    assert got == want
+    # the loss is summed with float atomics (order varies); the update itself is deterministic
+    assert np.allclose(got, want, rtol=1e-5, atol=0)
     assert torch.equal(net.get_params(), eager.get_params())
     eager.close()
     net.close()

@@ -39,8 +39,12 @@ def test_backward_matches_finite_differences():
 
 def test_gelu_closed_form():
     z = np.array([-3.0, -1.0, 0.0, 0.5, 2.0])
-    ref = [0.5 * x * (1 + math.erf(x / math.sqrt(2))) for x in z]
+    ref = [0.5 * x * (1 + math.tanh(math.sqrt(2 / math.pi) * (x + 0.044715 * x ** 3))) for x in z]
     assert np.allclose(mlp.gelu(z), ref, rtol=1e-15, atol=1e-300)
+    # the tanh form stays within 2e-3 of the erf form x (1 + erf(x / sqrt 2)) / 2
+    xs = np.linspace(-6, 6, 241)
+    erf_form = np.array([0.5 * x * (1 + math.erf(x / math.sqrt(2))) for x in xs])
+    assert np.abs(mlp.gelu(xs) - erf_form).max() < 2e-3
     h = 1e-6
     assert np.allclose(mlp.gelu_grad(z), (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h), rtol=1e-8, atol=1e-9)
     assert mlp.gelu(np.array([0.0]))[0] == 0.0
