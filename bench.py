@@ -31,7 +31,7 @@ METRIC = "M vertex-rotations/s and % of HBM/tensor roofline; BF16+surrogate vs F
 UNIT = "M vertex-rotations/s"
 WORKLOAD = ("RGB 128x256 lat-long lighting (32768 Haar coefficients per channel), 16 fractional "
             "shifts per frame, 50000 torus vertices (8 occluders), top-256 CSR FP32 transport "
-            "(repacked as 8-vertex group CSR)")
+            "(repacked as 4-vertex group CSR)")
 FLUSH_BYTES = 256 << 20
 
 
@@ -182,8 +182,8 @@ def algorithmic_bytes(wl):
     """Bytes a kernel must move at least, per launch: its stored input read
     once, the lighting read once, its output written once."""
     V, K, S, C, N = wl["V"], wl["K"], wl["S"], wl["C"], wl["H"] * wl["W"]
-    U, G = wl["union"], (wl["V"] + 7) // 8
-    gcsr = U * (8 * 4 + 2) + (G + 1) * 4 + N * S * C * 4 + V * S * C * 4
+    U, G = wl["union"], (wl["V"] + 3) // 4
+    gcsr = U * (4 * 4 + 2) + (G + 1) * 4 + N * S * C * 4 + V * S * C * 4
     csr = V * K * 4 + V * K * 2 + (V + 1) * 4 + N * S * C * 4 + V * S * C * 4
     shift = C * N * 4 + S * C * N * 4
     return {"k_shade_gcsr_f32": gcsr, "k_shade_csr_f32": csr, "k_shift": shift}

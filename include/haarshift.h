@@ -168,10 +168,10 @@ typedef enum {
   HAAR_T_BINCSR_F16_U32 = 3, /* vals [V][bins][K] binary16, idx [V][bins][K] uint32,
                                bin_of [S][V] uint8 selects the bin of (s, v) */
   HAAR_T_GCSR_F32_U16 = 4    /* vertex-group CSR made by haar_transport_group: groups of
-                               8 consecutive vertices share one sorted union index list
-                               idx (uint16) with values [nnz][8] float32 (0 where a
+                               4 consecutive vertices share one sorted union index list
+                               idx (uint16) with values [nnz][4] float32 (0 where a
                                vertex lacks the coefficient); rowptr = group offsets
-                               [ceil(V/8) + 1] int32 */
+                               [ceil(V/4) + 1] int32 */
 } haar_transport_kind_t;
 
 typedef struct {
@@ -208,14 +208,14 @@ HAAR_API haar_status_t shade_batch(haar_shift_plan_t plan, const float* coeffs_i
 
 /* Repack top-K CSR transport (rows sorted by index, rowptr int32 [V+1],
  * idx uint16, vals float32) into the vertex-group CSR of HAAR_T_GCSR_F32_U16:
- * the union of the indices of every 8 consecutive rows, sorted, with the
+ * the union of the indices of every 4 consecutive rows, sorted, with the
  * values of each row at its union positions (0 elsewhere).  A storage form
  * of the top-K (non-linear) approximation cited in Sec. "Haar-domain
  * methods": the double product is unchanged, each lighting row gathered
- * serves 8 vertices.  N: coefficients per map (<= 65536; indices >= N are
- * dropped).  gptr [ceil(V/8) + 1] int32 (device) receives the group offsets;
- * gptr[ceil(V/8)] is the total.  Call once with gidx = gvals = NULL to get
- * gptr, then again with gidx [total] uint16 and gvals [total][8] float32. */
+ * serves 4 vertices.  N: coefficients per map (<= 65536; indices >= N are
+ * dropped).  gptr [ceil(V/4) + 1] int32 (device) receives the group offsets;
+ * gptr[ceil(V/4)] is the total.  Call once with gidx = gvals = NULL to get
+ * gptr, then again with gidx [total] uint16 and gvals [total][4] float32. */
 HAAR_API haar_status_t haar_transport_group(int V, int N, const int32_t* rowptr, const uint16_t* idx,
                                             const float* vals, int32_t* gptr, uint16_t* gidx, float* gvals,
                                             void* stream);
@@ -237,8 +237,10 @@ HAAR_API haar_status_t haar_view_bins(int V, int S, int bins, const float* pos, 
  * transport).  A 4 x 256 GELU MLP (tanh-form GELU) maps a vertex's position, normal and view
  * direction to its transport coefficients at a fixed set of 512 canonical
  * indices (standardised: T_j = mu_j + sigma_j out_j).  Encoding of the 9
- * inputs: x, sin(w_f x), cos(w_f x) with w_f = pi 2^(f/2), f = 0..15, zero-padded
- * to 320.  Flat FP32 parameter vector (haar_mlp_param_count() floats):
+ * inputs (position p, normal n, view w) with w_f = pi 2^(f/2), f = 0..15:
+ * columns 0..199 = [p, n], per f sin(w_f [p, n]), cos(w_f [p, n]), 2 zeros;
+ * columns 200..298 = w, per f sin(w_f w), cos(w_f w); zeros to 320.
+ * Flat FP32 parameter vector (haar_mlp_param_count() floats):
  * W1[256][320] b1[256] W2[256][256] b2 W3 b3 W4 b4 Wo[512][256] bo[512].
  * Forward and backward run as bf16 tcgen05 GEMMs with FP32 accumulation;
  * master weights and Adam state are FP32.  A surrogate owns its device

@@ -4,9 +4,12 @@ Not part of the paper: a learned stand-in for stored transport.  It maps a
 vertex's position, normal and view direction (9 numbers) to the Haar
 transport coefficients at a fixed index set:
 
-* encoding: the 9 inputs, then sin and cos of omega_f * input for 16
-  frequencies omega_f = pi * 2^(f/2), f = 0..15 (297 features), zero-padded
-  to 320;
+* encoding of the 9 inputs (position p, normal n, view direction w) with 16
+  frequencies omega_f = pi * 2^(f/2), f = 0..15, laid out so that the part
+  that depends on the vertex alone comes first:
+  [p, n] (6), then per f: sin(omega_f [p, n]) (6), cos(omega_f [p, n]) (6),
+  2 zeros (columns 0..199); w (3), then per f: sin(omega_f w) (3),
+  cos(omega_f w) (3) (columns 200..298); zeros to 320 (297 features);
 * 4 hidden layers of width 256 with GELU in its tanh form (Hendrycks and
   Gimpel 2016): gelu(z) = z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) / 2;
 * a linear output layer of width 512 (standardised coefficients);
@@ -29,6 +32,7 @@ from .transport import to_bf16
 N_RAW = 9
 N_FREQ = 16
 N_ENC = N_RAW + 2 * N_FREQ * N_RAW     # 297
+N_VERTEX_COLS = 200                    # columns that depend on the vertex alone
 N_IN = 320
 WIDTH = 256
 DEPTH = 4
@@ -41,15 +45,19 @@ def omegas() -> np.ndarray:
 
 
 def encode(raw: np.ndarray) -> np.ndarray:
-    """[B, 9] -> [B, 320]: raw, then per frequency sin(w x) (9) and cos(w x) (9)."""
+    """[B, 9] (p, n, w) -> [B, 320] in the layout of the module docstring."""
     raw = np.asarray(raw, dtype=np.float64)
     B = raw.shape[0]
     out = np.zeros((B, N_IN))
-    out[:, :N_RAW] = raw
-    for f, w in enumerate(omegas()):
-        o = N_RAW + 2 * N_RAW * f
-        out[:, o:o + N_RAW] = np.sin(w * raw)
-        out[:, o + N_RAW:o + 2 * N_RAW] = np.cos(w * raw)
+    pn, w = raw[:, :6], raw[:, 6:9]
+    out[:, 0:6] = pn
+    for f, om in enumerate(omegas()):
+        out[:, 6 + 12 * f:12 + 12 * f] = np.sin(om * pn)
+        out[:, 12 + 12 * f:18 + 12 * f] = np.cos(om * pn)
+    out[:, 200:203] = w
+    for f, om in enumerate(omegas()):
+        out[:, 203 + 6 * f:206 + 6 * f] = np.sin(om * w)
+        out[:, 206 + 6 * f:209 + 6 * f] = np.cos(om * w)
     return out
 
 

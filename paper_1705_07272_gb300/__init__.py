@@ -44,6 +44,7 @@ HAAR_T_DENSE_BF16 = 1
 HAAR_T_CSR_F32_U16 = 2
 HAAR_T_BINCSR_F16_U32 = 3
 HAAR_T_GCSR_F32_U16 = 4
+GROUP = 4            # vertices per group of HAAR_T_GCSR_F32_U16
 
 EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward",
            "haar_inverse", "shade_vertices", "shade_batch", "haar_view_bins",
@@ -283,14 +284,14 @@ def shade_batch(plan: Plan, coeffs_in, params, transport: Transport, radiance=No
 def haar_transport_group(V, N, rowptr, idx, vals, stream=None):
     """Vertex-group CSR (Transport of kind HAAR_T_GCSR_F32_U16) from top-K CSR."""
     import torch
-    G = (V + 7) // 8
+    G = (V + GROUP - 1) // GROUP
     gptr = torch.empty(G + 1, dtype=torch.int32, device=rowptr.device)
     st = _stream(stream)
     _check(lib().haar_transport_group(V, N, _dev(rowptr, torch.int32, "rowptr"), _dev(idx, None, "idx"),
                                       _dev(vals, torch.float32, "vals"), gptr.data_ptr(), None, None, st))
     total = int(gptr[-1].item())
     gidx = torch.empty(max(total, 1), dtype=torch.int16, device=rowptr.device)
-    gvals = torch.empty((max(total, 1), 8), dtype=torch.float32, device=rowptr.device)
+    gvals = torch.empty((max(total, 1), GROUP), dtype=torch.float32, device=rowptr.device)
     _check(lib().haar_transport_group(V, N, rowptr.data_ptr(), idx.data_ptr(), vals.data_ptr(), gptr.data_ptr(),
                                       gidx.data_ptr(), gvals.data_ptr(), st))
     return Transport(HAAR_T_GCSR_F32_U16, V, 0, gvals, gidx, gptr)

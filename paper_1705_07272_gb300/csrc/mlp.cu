@@ -47,6 +47,8 @@ struct EpiArgs {
   const float* beff;       // EPI_SHADE: [groups][C]
   int rows_per_group, groups, C, row0;
   float* radiance;         // EPI_SHADE: R[v][s][c], row m + row0 = s * rows_per_group + v
+  float* split_ws;         // EPI_F32 split-K partial sums [splits][M][N] (null: no split)
+  long long split_ws_floats;
 };
 
 // GELU in its tanh form (Hendrycks and Gimpel 2016), with the hardware tanh
@@ -83,6 +85,8 @@ template <int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
 k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K, int BN,
        int STAGES, int tmem_cols, EpiArgs e, int* status) {
+  // split-K: CTA z accumulates k-blocks [z * kbs, (z + 1) * kbs); EPI_F32 adds
+  // its partial sums atomically into a zeroed output
   using namespace tc;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ GBars bars;
@@ -90,7 +94,9 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)BN * BK * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  const int kblocks = K / BK;
+  const int kbs = (K / BK + gridDim.z - 1) / gridDim.z;
+  const int kb0 = blockIdx.z * kbs;
+  const int kblocks = min(kbs, K / BK - kb0);
   const int tm = blockIdx.x, tn = blockIdx.y;
   volatile int* abort_flag = &bars.abort_flag;
 
@@ -127,8 +133,8 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
         const uint32_t sa = base + stage * stage_bytes;
         const uint32_t fb = smem_u32(&bars.full[stage]);
         mbar_arrive_tx(fb, stage_bytes);
-        tma_load_2d(sa, &mapA, kb * BK, tm * BM, fb);
-        tma_load_2d(sa + a_bytes, &mapB, kb * BK, tn * BN, fb);
+        tma_load_2d(sa, &mapA, (kb0 + kb) * BK, tm * BM, fb);
+        tma_load_2d(sa + a_bytes, &mapB, (kb0 + kb) * BK, tn * BN, fb);
         issued[stage] = 1;
         issued_phase[stage] = phase;
         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -183,7 +189,11 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
         tmem_ld16(t_row + (uint32_t)c0, v);
         const int n0 = tn * BN + c0;
         if (EPI == EPI_F32) {
-          if (row_ok) {
+          if (row_ok && gridDim.z > 1) {
+            float* dst = e.split_ws + ((long long)blockIdx.z * e.M + m) * e.N + n0;
+            for (int i = 0; i < 16; ++i)
+              if (n0 + i < e.N) dst[i] = v[i];
+          } else if (row_ok) {
             float* dst = e.out_f32 + (long long)m * e.ld_f32 + n0;
             if (n0 + 16 <= e.N && (e.ld_f32 & 3) == 0) {
 #pragma unroll
@@ -264,18 +274,40 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
 
 // -------------------------------------------------------------- helper kernels
 
-__device__ __forceinline__ void encode_row(const float raw[N_RAW], __nv_bfloat16* out, int lane) {
-  // lanes 0..143 (in steps of 32) take one (frequency, input) pair: sin and cos together
-  for (int t = lane; t < N_FREQ * N_RAW; t += 32) {
-    const int f = t / N_RAW, r = t - f * N_RAW;
-    const float w = 3.14159265358979323846f * exp2f(0.5f * (float)f);
+// Encoding layout: [p, n] (6); per f: sin(w_f [p, n]) (6), cos(w_f [p, n]) (6);
+// 2 zeros (columns 0..199 depend on the vertex alone); view w (3); per f:
+// sin(w_f w) (3), cos(w_f w) (3) (columns 200..298); zeros to 320.
+constexpr int N_VCOLS = 200;
+
+__device__ __forceinline__ float omega(int f) { return 3.14159265358979323846f * exp2f(0.5f * (float)f); }
+
+__device__ __forceinline__ void encode_vertex_part(const float pn[6], __nv_bfloat16* out, int lane) {
+  for (int t = lane; t < N_FREQ * 6; t += 32) {
+    const int f = t / 6, r = t - f * 6;
     float sv, cv;
-    sincosf(w * raw[r], &sv, &cv);
-    out[N_RAW + 2 * N_RAW * f + r] = __float2bfloat16_rn(sv);
-    out[N_RAW + 2 * N_RAW * f + N_RAW + r] = __float2bfloat16_rn(cv);
+    sincosf(omega(f) * pn[r], &sv, &cv);
+    out[6 + 12 * f + r] = __float2bfloat16_rn(sv);
+    out[12 + 12 * f + r] = __float2bfloat16_rn(cv);
   }
-  if (lane < N_RAW) out[lane] = __float2bfloat16_rn(raw[lane]);
-  for (int j = N_RAW + 2 * N_FREQ * N_RAW + lane; j < N_IN; j += 32) out[j] = __float2bfloat16_rn(0.0f);
+  if (lane < 6) out[lane] = __float2bfloat16_rn(pn[lane]);
+  if (lane < 2) out[198 + lane] = __float2bfloat16_rn(0.0f);
+}
+
+__device__ __forceinline__ void encode_view_part(const float w[3], __nv_bfloat16* out, int lane) {
+  for (int t = lane; t < N_FREQ * 3; t += 32) {
+    const int f = t / 3, r = t - f * 3;
+    float sv, cv;
+    sincosf(omega(f) * w[r], &sv, &cv);
+    out[203 + 6 * f + r] = __float2bfloat16_rn(sv);
+    out[206 + 6 * f + r] = __float2bfloat16_rn(cv);
+  }
+  if (lane < 3) out[200 + lane] = __float2bfloat16_rn(w[lane]);
+  for (int j = 299 + lane; j < N_IN; j += 32) out[j] = __float2bfloat16_rn(0.0f);
+}
+
+__device__ __forceinline__ void encode_row(const float raw[N_RAW], __nv_bfloat16* out, int lane) {
+  encode_vertex_part(raw, out, lane);
+  encode_view_part(raw + 6, out, lane);
 }
 
 // X[b][320] from raw inputs [b][9]
@@ -320,6 +352,17 @@ __global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int R, int C, 
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (r < R && c < C) out[(long long)c * R + r] = t[threadIdx.x][i];
   }
+}
+
+// out[m][n] (row stride ld) = bias[n] + sum_z ws[z][m][n], fixed order
+__global__ void k_split_reduce(const float* __restrict__ ws, int splits, int M, int N, const float* __restrict__ bias,
+                               float* __restrict__ out, int ld) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)M * N) return;
+  const int m = (int)(i / N), n = (int)(i - (long long)m * N);
+  float acc = bias ? bias[n] : 0.0f;
+  for (int z = 0; z < splits; ++z) acc += ws[(long long)z * M * N + i];
+  out[(long long)m * ld + n] = acc;
 }
 
 // dOut = bf16(2 (out - y) / (B N)); loss += mean((out - y)^2)
@@ -399,32 +442,324 @@ __global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ 
 // Output layer folded into the lighting, per group s:
 //   Weff[s][i][c] = sum_j Wo[j][i] sigma_j L(s, c, idx_j)
 //   beff[s][c]    = sum_j (mu_j + sigma_j bo_j) L(s, c, idx_j)
-__global__ void k_fold(const float* __restrict__ p, const float* __restrict__ mu, const float* __restrict__ sigma,
-                       const int* __restrict__ idx, const float* __restrict__ L, long long st_s, long long st_c,
-                       long long st_k, int S, int C, float* __restrict__ weff, float* __restrict__ beff) {
-  const int s = blockIdx.x;
+// Block (s, ib) computes i in [32 ib, 32 ib + 32): lane = i, warp = a slice of j.
+__global__ void __launch_bounds__(256) k_fold(const float* __restrict__ p, const float* __restrict__ mu,
+                                              const float* __restrict__ sigma, const int* __restrict__ idx,
+                                              const float* __restrict__ L, long long st_s, long long st_c,
+                                              long long st_k, int S, int C, float* __restrict__ weff,
+                                              float* __restrict__ beff) {
+  const int s = blockIdx.x, ib = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float* Wo = p + w_off(N_LAYERS - 1);
   const float* bo = p + b_off(N_LAYERS - 1);
   __shared__ float sl[N_OUT][4];
+  __shared__ float part[8][32][4];
   for (int j = threadIdx.x; j < N_OUT; j += blockDim.x)
     for (int c = 0; c < 4; ++c)
       sl[j][c] = (c < C) ? sigma[j] * L[s * st_s + c * st_c + (long long)idx[j] * st_k] : 0.0f;
   __syncthreads();
-  for (int t = threadIdx.x; t < WIDTH * C; t += blockDim.x) {
-    const int i = t / C, c = t - i * C;
-    float acc = 0.0f;
-    for (int j = 0; j < N_OUT; ++j) acc = fmaf(Wo[(long long)j * WIDTH + i], sl[j][c], acc);
-    weff[((long long)s * WIDTH + i) * C + c] = acc;
+  const int i = ib * 32 + lane;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int j = warp * (N_OUT / 8); j < (warp + 1) * (N_OUT / 8); ++j) {
+    const float w = Wo[(long long)j * WIDTH + i];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = fmaf(w, sl[j][c], acc[c]);
   }
-  if (threadIdx.x < C) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) part[warp][lane][c] = acc[c];
+  __syncthreads();
+  if (warp == 0) {
+    for (int c = 0; c < C; ++c) {
+      float t = 0.0f;
+      for (int w8 = 0; w8 < 8; ++w8) t += part[w8][lane][c];
+      weff[((long long)s * WIDTH + i) * C + c] = t;
+    }
+  }
+  if (ib == 0 && threadIdx.x < C) {
     const int c = threadIdx.x;
-    float acc = 0.0f;
+    float t = 0.0f;
     for (int j = 0; j < N_OUT; ++j) {
       const float lj = L[s * st_s + c * st_c + (long long)idx[j] * st_k];
-      acc = fmaf(mu[j] + sigma[j] * bo[j], lj, acc);
+      t = fmaf(mu[j] + sigma[j] * bo[j], lj, t);
     }
-    beff[s * C + c] = acc;
+    beff[s * C + c] = t;
   }
+}
+
+// ----------------------------------------------------------- fused surrogate shading
+// Persistent, one CTA per SM, 10 warps, one 128-row tile at a time (rows are
+// (shift, vertex) pairs, row = s * V + v):
+//   warp 0     TMA producer: the weight k-blocks [256 x 64] of W1..W4 into a
+//              3-stage ring, in the order the MMAs use them, tile after tile;
+//   warp 1     TMEM allocator and MMA issuer (M = 128, N = 256, K = 16);
+//   warps 2-9  encode the tile into the activation buffer (the 200
+//              per-vertex columns copied from a table, the view columns
+//              computed), then each layer's epilogue: bias + GELU, written
+//              back as the next layer's bf16 A operand in the same
+//              128-byte-swizzled K-major layout the tensor core reads; the
+//              last layer's epilogue takes the double product with the output
+//              layer folded into the lighting.  Activations never leave the SM.
+constexpr int F_THREADS = 320;
+constexpr int F_STAGES = 3;
+constexpr uint32_t F_ACT_BYTES = 5 * 16384;  // 128 rows x 320 bf16
+constexpr uint32_t F_W_BYTES = 256 * 128;    // one weight k-block [256 x 64] bf16
+
+struct __align__(8) FBars {
+  uint64_t wfull[F_STAGES], wempty[F_STAGES];
+  uint64_t tfull, aready, drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+struct FusedArgs {
+  int V, S, C;
+  long long rows;
+  const __nv_bfloat16* vfeat;  // [V][200]
+  const float* pos;            // [V][3]
+  const float* cams;           // [S][3]
+  const float* params;         // flat parameters (biases)
+  const float* weff;           // [S][256][C]
+  const float* beff;           // [S][C]
+  float* radiance;             // [V][S][C], zeroed before the launch
+};
+
+// byte offset of element (r, c) in the activation buffer: k-block c/64 is a
+// [128 rows x 128 B] tile, rows in 1024-byte groups of 8, 16-byte chunk
+// (c % 64) / 8 stored at chunk ^ (r % 8)
+__device__ __forceinline__ uint32_t act_off(int r, int c) {
+  const int ch = (c & 63) >> 3;
+  return (uint32_t)((c >> 6) * 16384 + (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4) + ((c & 7) << 1));
+}
+
+__global__ void __launch_bounds__(F_THREADS, 1)
+k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUtensorMap w1,
+            const __grid_constant__ CUtensorMap w2, const __grid_constant__ CUtensorMap w3, FusedArgs f,
+            int* status) {
+  using namespace tc;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ FBars bars;
+  __shared__ int rinfo[8][16][2];
+  __shared__ float rview[8][16][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* act = smem_raw + (base - smem_u32(smem_raw));
+  const uint32_t act_s = base;
+  const uint32_t ring = base + F_ACT_BYTES;
+  const long long n_tiles = (f.rows + BM - 1) / BM;
+  volatile int* abort_flag = &bars.abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < F_STAGES; ++i) {
+      mbar_init(smem_u32(&bars.wfull[i]), 1);
+      mbar_init(smem_u32(&bars.wempty[i]), 1);
+    }
+    mbar_init(smem_u32(&bars.tfull), 1);
+    mbar_init(smem_u32(&bars.aready), 8);
+    mbar_init(smem_u32(&bars.drain), 1);
+    bars.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&bars.tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = bars.tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued[F_STAGES];
+      uint32_t issued_phase[F_STAGES];
+      for (int i = 0; i < F_STAGES; ++i) { issued[i] = 0; issued_phase[i] = 0; }
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int l = 0; l < 4 && ok; ++l) {
+          const CUtensorMap* map = (l == 0) ? &w0 : (l == 1) ? &w1 : (l == 2) ? &w2 : &w3;
+          const int nk = (l == 0) ? 5 : 4;
+          for (int kb = 0; kb < nk; ++kb) {
+            if (!mbar_wait(smem_u32(&bars.wempty[stage]), phase ^ 1u, status, abort_flag)) { ok = false; break; }
+            const uint32_t fb = smem_u32(&bars.wfull[stage]);
+            mbar_arrive_tx(fb, F_W_BYTES);
+            tma_load_2d(ring + stage * F_W_BYTES, map, kb * BK, 0, fb);
+            issued[stage] = 1;
+            issued_phase[stage] = phase;
+            if (++stage == F_STAGES) { stage = 0; phase ^= 1u; }
+          }
+        }
+      }
+      for (int i = 0; i < F_STAGES; ++i) {
+        if (!issued[i]) continue;
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try(smem_u32(&bars.wfull[i]), issued_phase[i]) && gtimer() - t0 < TIMEOUT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, 256);
+      int stage = 0;
+      uint32_t phase = 0;
+      long long step = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int l = 0; l < 4 && ok; ++l, ++step) {
+          if (!mbar_wait(smem_u32(&bars.aready), (uint32_t)(step & 1), status, abort_flag)) { ok = false; break; }
+          fence_after();
+          const int nk = (l == 0) ? 5 : 4;
+          for (int kb = 0; kb < nk; ++kb) {
+            if (!mbar_wait(smem_u32(&bars.wfull[stage]), phase, status, abort_flag)) { ok = false; break; }
+            fence_after();
+            const uint32_t wa = ring + stage * F_W_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / UMMA_K; ++k)
+              mma_bf16(tmem, make_desc(act_s + kb * 16384 + k * UMMA_K * 2), make_desc(wa + k * UMMA_K * 2), idesc,
+                       (kb | k) != 0 ? 1u : 0u);
+            mma_commit(smem_u32(&bars.wempty[stage]));
+            if (++stage == F_STAGES) { stage = 0; phase ^= 1u; }
+          }
+          if (ok) mma_commit(smem_u32(&bars.tfull));
+        }
+      }
+      mma_commit(smem_u32(&bars.drain));
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try(smem_u32(&bars.drain), 0) && gtimer() - t0 < TIMEOUT_NS) {
+      }
+    }
+  } else {
+    const int wid = warp - 2;                 // 0..7
+    const int q = warp & 3;                   // TMEM lane quarter
+    const int half = wid >> 2;                // column half
+    long long step = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      const long long row0 = t * BM;
+      // ---- encode 16 rows per warp: row info first, then many independent
+      // loads / sincos per lane (lanes sweep (row, chunk) pairs)
+      const int r0 = wid * 16;
+      if (lane < 16) {
+        const long long row = row0 + r0 + lane;
+        int sr = -1, vr = 0;
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+        if (row < f.rows) {
+          sr = (int)(row / f.V);
+          vr = (int)(row - (long long)sr * f.V);
+          const float wx = __ldg(f.cams + 3 * sr) - __ldg(f.pos + 3 * vr);
+          const float wy = __ldg(f.cams + 3 * sr + 1) - __ldg(f.pos + 3 * vr + 1);
+          const float wz = __ldg(f.cams + 3 * sr + 2) - __ldg(f.pos + 3 * vr + 2);
+          const float inv = rsqrtf(wx * wx + wy * wy + wz * wz);
+          w0 = wx * inv; w1 = wy * inv; w2 = wz * inv;
+        }
+        rinfo[wid][lane][0] = sr;
+        rinfo[wid][lane][1] = vr;
+        rview[wid][lane][0] = w0;
+        rview[wid][lane][1] = w1;
+        rview[wid][lane][2] = w2;
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int e = lane; e < 16 * 25; e += 32) {
+        const int i = e / 25, ch = e - i * 25;
+        const int sr = rinfo[wid][i][0];
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (sr >= 0) val = __ldg(reinterpret_cast<const uint4*>(f.vfeat + (long long)rinfo[wid][i][1] * N_VCOLS) + ch);
+        *reinterpret_cast<uint4*>(act + act_off(r0 + i, 8 * ch)) = val;
+      }
+#pragma unroll 4
+      for (int e = lane; e < 16 * N_FREQ * 3; e += 32) {
+        const int i = e / (N_FREQ * 3), t2 = e - i * (N_FREQ * 3);
+        const int fq = t2 / 3, rr = t2 - fq * 3;
+        float sv = 0.0f, cv = 0.0f;
+        if (rinfo[wid][i][0] >= 0) sincosf(omega(fq) * rview[wid][i][rr], &sv, &cv);
+        *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, 203 + 6 * fq + rr)) = __float2bfloat16_rn(sv);
+        *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, 206 + 6 * fq + rr)) = __float2bfloat16_rn(cv);
+      }
+      for (int e = lane; e < 16 * 24; e += 32) {       // raw view (3) and the zero pad (21)
+        const int i = e / 24, j = e - i * 24;
+        const float x = (j < 3 && rinfo[wid][i][0] >= 0) ? rview[wid][i][j] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, (j < 3) ? 200 + j : 296 + j)) = __float2bfloat16_rn(x);
+      }
+      fence_before();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars.aready));
+      // ---- layers
+      const int r = q * 32 + lane;
+      const long long row = row0 + r;
+      const bool row_ok = row < f.rows;
+      for (int l = 0; l < 4; ++l, ++step) {
+        if (!mbar_wait(smem_u32(&bars.tfull), (uint32_t)(step & 1), status, abort_flag)) { ok = false; break; }
+        fence_after();
+        const float* bias = f.params + b_off(l);
+        float acc_c[4] = {0.f, 0.f, 0.f, 0.f};
+        int s = 0;
+        if (l == 3 && row_ok) s = (int)(row / f.V);
+        const float* W = f.weff + (long long)s * WIDTH * f.C;
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c0 = half * 128 + cc * 32;
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          if (l < 3) {
+            uint32_t pk[16];
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+              __nv_bfloat162 hb = __floats2bfloat162_rn(gelu(v[i] + __ldg(bias + c0 + i)),
+                                                        gelu(v[i + 1] + __ldg(bias + c0 + i + 1)));
+              pk[i >> 1] = *reinterpret_cast<uint32_t*>(&hb);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              *reinterpret_cast<uint4*>(act + act_off(r, c0 + 8 * j)) =
+                  make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float h = gelu(v[i] + __ldg(bias + c0 + i));
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (c < f.C) acc_c[c] = fmaf(h, __ldg(W + (long long)(c0 + i) * f.C + c), acc_c[c]);
+            }
+          }
+        }
+        fence_before();
+        if (l < 3) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars.aready));
+        } else if (row_ok) {
+          // the two column halves add into the zeroed output (two adds onto
+          // zero commute exactly, so the result does not depend on their order)
+          const int vv = (int)(row - (long long)s * f.V);
+          for (int c = 0; c < f.C; ++c)
+            atomicAdd(f.radiance + ((long long)vv * f.S + s) * f.C + c,
+                      acc_c[c] + (half == 0 ? f.beff[s * f.C + c] : 0.0f));
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  }
+}
+
+// per-vertex part of the encoding: vfeat[v][0..199]
+__global__ void k_vertex_features(const float* __restrict__ pos, const float* __restrict__ nrm, int V,
+                                  __nv_bfloat16* __restrict__ vfeat) {
+  const int v = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (v >= V) return;
+  float pn[6];
+  for (int i = 0; i < 3; ++i) {
+    pn[i] = pos[3 * v + i];
+    pn[3 + i] = nrm[3 * v + i];
+  }
+  encode_vertex_part(pn, vfeat + (long long)v * N_VCOLS, threadIdx.x & 31);
 }
 
 }  // namespace mlpk
@@ -453,6 +788,8 @@ struct haar_mlp_s {
   __nv_bfloat16* tB;  // transpose scratch [320][B]
   float* loss;        // [1]
   int* step;          // [1] Adam step count
+  float* split_ws;    // split-K partial sums of the weight gradients
+  long long split_ws_floats;
   // inference buffers (max_rows rows)
   __nv_bfloat16* iX;  // [rows][320]
   __nv_bfloat16* ih0; // [rows][256]
@@ -481,10 +818,20 @@ static haar_status_t gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B,
                           int* status, cudaStream_t st) {
   using namespace tc;
   if (K % BK != 0) return set_error(HAAR_ERR_INVALID_ARG, "mlp gemm: K = %d is not a multiple of 64", K);
-  const int ntiles = (N + 255) / 256;
+  int ntiles = (N + 255) / 256;
+  const int mtiles = (M + BM - 1) / BM;
+  if (EPI != EPI_SHADE && mtiles * ntiles < 152 && N >= 256) ntiles = (N + 127) / 128;   // more CTAs
   int BN = (N + ntiles - 1) / ntiles;
   BN = (BN + 15) / 16 * 16;
   if (EPI == EPI_SHADE && ntiles != 1) return set_error(HAAR_ERR_UNSUPPORTED, "mlp gemm: shade epilogue needs N <= 256");
+  // split K for small outputs with long K (weight gradients: K = batch)
+  int ksplit = 1;
+  if (EPI == EPI_F32 && e.split_ws != nullptr) {
+    const int tiles = mtiles * ((N + BN - 1) / BN);
+    const int kb = K / BK;
+    while (ksplit * 2 * tiles <= 2 * 152 && kb / (ksplit * 2) >= 4 && kb % (ksplit * 2) == 0 &&
+           (long long)ksplit * 2 * M * N <= e.split_ws_floats) ksplit *= 2;
+  }
   CUtensorMap mA, mB;
   if (!encode_2d(&mA, A, (uint64_t)K, (uint64_t)M, BK, BM) || !encode_2d(&mB, B, (uint64_t)K, (uint64_t)N, BK, (uint32_t)BN))
     return set_error(HAAR_ERR_CUDA, "mlp gemm: cuTensorMapEncodeTiled failed");
@@ -493,7 +840,7 @@ static haar_status_t gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B,
   const size_t stage = (size_t)BM * BK * 2 + (size_t)BN * BK * 2;
   // two stages (two CTAs per SM overlap one's epilogue with the other's
   // main loop); the bf16 epilogue stages its rows in the same memory
-  int stages = K / BK < 2 ? 1 : 2;
+  int stages = K / BK / ksplit < 2 ? 1 : 2;
   size_t ring = (size_t)stages * stage;
   const size_t staging = (size_t)4 * 32 * ((size_t)BN * 2 + 16);
   if (ring < staging) ring = staging;
@@ -502,9 +849,13 @@ static haar_status_t gemm(const __nv_bfloat16* A, int M, const __nv_bfloat16* B,
   while (tcols < BN) tcols <<= 1;
   cudaError_t err = cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return cuda_check(err, "cudaFuncSetAttribute(k_gemm)");
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, ksplit);
   k_gemm<EPI><<<grid, THREADS, smem, st>>>(mA, mB, K, BN, stages, tcols, e, status);
-  return cuda_check(cudaGetLastError(), "k_gemm launch");
+  haar_status_t r = cuda_check(cudaGetLastError(), "k_gemm launch");
+  if (r != HAAR_OK || ksplit == 1) return r;
+  const long long n = (long long)M * N;
+  k_split_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e.split_ws, ksplit, M, N, e.bias, e.out_f32, e.ld_f32);
+  return cuda_check(cudaGetLastError(), "k_split_reduce launch");
 }
 
 static EpiArgs epi(int M, int N) {
@@ -559,6 +910,8 @@ static haar_status_t backward(haar_mlp_s* M, int B, const float* target, cudaStr
     EpiArgs e = epi(N_OUT, WIDTH);
     e.out_f32 = M->g + w_off(4);
     e.ld_f32 = WIDTH;
+    e.split_ws = M->split_ws;
+    e.split_ws_floats = M->split_ws_floats;
     HS_TRY(gemm<EPI_F32>(M->tA, N_OUT, M->tB, WIDTH, B, e, M->status, st));
   }
   k_colsum<<<(N_OUT + 31) / 32, 256, 0, st>>>(M->dout, B, N_OUT, M->g + b_off(4));
@@ -581,6 +934,8 @@ static haar_status_t backward(haar_mlp_s* M, int B, const float* target, cudaStr
     EpiArgs e = epi(WIDTH, fin);
     e.out_f32 = M->g + w_off(l);
     e.ld_f32 = fin;
+    e.split_ws = M->split_ws;
+    e.split_ws_floats = M->split_ws_floats;
     HS_TRY(gemm<EPI_F32>(M->tA, WIDTH, M->tB, fin, B, e, M->status, st));
     k_colsum<<<(WIDTH + 31) / 32, 256, 0, st>>>(dz, B, WIDTH, M->g + b_off(l));
     HS_TRY(cuda_check(cudaGetLastError(), "k_colsum launch"));
@@ -618,7 +973,7 @@ static void mlp_free(haar_mlp_s* M) {
   if (!M) return;
   void* ptrs[] = {M->p, M->g, M->m, M->v, M->wb, M->wt, M->X, M->h[0], M->h[1], M->h[2], M->h[3], M->z[0],
                   M->z[1], M->z[2], M->z[3], M->out, M->dout, M->dz, M->dz2, M->tA, M->tB, M->loss, M->iX,
-                  M->ih0, M->ih1, M->weff, M->beff, M->status, M->step};
+                  M->ih0, M->ih1, M->weff, M->beff, M->status, M->step, M->split_ws};
   for (void* q : ptrs) cudaFree(q);
   delete M;
 }
@@ -671,6 +1026,8 @@ haar_status_t haar_mlp_create(int max_batch, int max_rows, int max_groups, haar_
   ALLOC(M->beff, (size_t)max_groups * 4 * 4);
   ALLOC(M->status, 16);
   ALLOC(M->step, 16);
+  M->split_ws_floats = (long long)(max_batch / 256 > 1 ? max_batch / 256 : 1) * N_OUT * WIDTH;
+  ALLOC(M->split_ws, (size_t)M->split_ws_floats * 4);
 #undef ALLOC
   if (e != cudaSuccess) {
     mlp_free(M);
@@ -780,9 +1137,42 @@ haar_status_t haar_mlp_shade(haar_mlp_t M, int V, int S, const float* pos, const
   if (V < 1 || S < 1 || S > M->max_groups || C < 1 || C > 4)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_mlp_shade: V=%d S=%d (max %d) C=%d (1..4)", V, S, M->max_groups, C);
   cudaStream_t st = (cudaStream_t)stream;
-  k_fold<<<S, 256, 0, st>>>(M->p, mu, sigma, idx, lighting, st_s, st_c, st_k, S, C, M->weff, M->beff);
+  k_fold<<<dim3(S, WIDTH / 32), 256, 0, st>>>(M->p, mu, sigma, idx, lighting, st_s, st_c, st_k, S, C, M->weff,
+                                              M->beff);
   HS_TRY(cuda_check(cudaGetLastError(), "k_fold launch"));
   const long long rows = (long long)V * S;
+  if ((long long)V * N_VCOLS <= (long long)M->max_rows * N_IN) {
+    // fused: per-vertex features once, then every layer on chip
+    k_vertex_features<<<(V + 7) / 8, 256, 0, st>>>(pos, nrm, V, M->iX);
+    HS_TRY(cuda_check(cudaGetLastError(), "k_vertex_features launch"));
+    HS_TRY(cuda_check(cudaMemsetAsync(radiance, 0, sizeof(float) * (size_t)rows * C, st), "haar_mlp_shade: zero radiance"));
+    CUtensorMap wm[4];
+    for (int l = 0; l < 4; ++l)
+      if (!encode_2d(&wm[l], M->wb + wb_off(l), (uint64_t)fan_in(l), (uint64_t)WIDTH, tc::BK, WIDTH))
+        return set_error(HAAR_ERR_CUDA, "haar_mlp_shade: cuTensorMapEncodeTiled failed");
+    FusedArgs fa;
+    fa.V = V;
+    fa.S = S;
+    fa.C = C;
+    fa.rows = rows;
+    fa.vfeat = M->iX;
+    fa.pos = pos;
+    fa.cams = cams;
+    fa.params = M->p;
+    fa.weff = M->weff;
+    fa.beff = M->beff;
+    fa.radiance = radiance;
+    const size_t smem = F_ACT_BYTES + (size_t)F_STAGES * F_W_BYTES + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_mlp_fused)");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (rows + 127) / 128;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    k_mlp_fused<<<grid, F_THREADS, smem, st>>>(wm[0], wm[1], wm[2], wm[3], fa, M->status);
+    return cuda_check(cudaGetLastError(), "k_mlp_fused launch");
+  }
   for (long long r0 = 0; r0 < rows; r0 += M->max_rows) {
     const int n = (int)((rows - r0) < M->max_rows ? (rows - r0) : M->max_rows);
     k_encode_scene<<<(n + 7) / 8, 256, 0, st>>>(pos, nrm, cams, V, r0, n, M->iX);

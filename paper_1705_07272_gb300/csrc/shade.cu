@@ -119,108 +119,77 @@ __global__ void __launch_bounds__(256) k_shade_csr_f32(const float* __restrict__
 }
 
 // ---------------------------------------------------------------- bin-CSR FP16
-// A CTA takes 16 vertices and walks the shifts s in order, so all its warps
-// gather from the same shifted lighting L[s] (L1-resident: the top-K indices
-// of a vertex stay within the coarse levels) while the 16 vertices' bin rows
-// stay in L2 across shifts.  Each lane reads 16 consecutive entries of a bin
-// row with vector loads (2 x 16 B of halves, 4 x 16 B of indices).
-// Lighting layout L[s][k][c] (channels interleaved), NL coefficients per (s, c).
-constexpr int kBinVerts = 16;
-
+// One warp per (vertex, s), s fastest, so the bin rows of one vertex are reused
+// across its shifts from L1.  Lanes take interleaved entries (lane + 32 i):
+// the row is sorted by coefficient index, so each warp-wide gather touches
+// neighbouring lighting rows L[s][k][c] (channels interleaved), NL
+// coefficients per (s, c).
 __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restrict__ vals,
                                                           const uint32_t* __restrict__ idx,
                                                           const uint8_t* __restrict__ bin_of, int V,
                                                           int bins, int K, int S, int C,
                                                           const float* __restrict__ L, long long NL,
                                                           float* __restrict__ R) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int v0 = blockIdx.x * kBinVerts;
-  const bool vec = (K % 512) == 0;                      // 16 entries per lane per 512-entry slab
-  for (int s = 0; s < S; ++s) {
-    const float* Ls = L + (long long)s * NL * C;
-    for (int vi = w; vi < kBinVerts; vi += 8) {
-      const int v = v0 + vi;
-      if (v >= V) break;
-      const int b = __ldg(bin_of + (long long)s * V + v);
-      const long long row = ((long long)v * bins + b) * K;
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      if (vec) {
-        for (int j0 = 16 * lane; j0 < K; j0 += 512) {
-          const uint4 h0 = __ldg(reinterpret_cast<const uint4*>(vals + row + j0));
-          const uint4 h1 = __ldg(reinterpret_cast<const uint4*>(vals + row + j0 + 8));
-          uint4 ix[4];
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (long long)V * S) return;
+  const int v = (int)(warp / S), s = (int)(warp - (long long)v * S);
+  const int b = __ldg(bin_of + (long long)s * V + v);
+  const long long row = ((long long)v * bins + b) * K;
+  const float* Ls = L + (long long)s * NL * C;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (int j = lane; j < K; j += 32) {
+    const long long k0 = __ldg(idx + row + j);
+    const bool ok = k0 < NL;                                // out-of-range entries are ignored
+    const float t = ok ? __half2float(vals[row + j]) : 0.0f;
+    const float* lk = Ls + (ok ? k0 : 0) * C;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) ix[i] = __ldg(reinterpret_cast<const uint4*>(idx + row + j0 + 4 * i));
-          const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-          const uint32_t kw[16] = {ix[0].x, ix[0].y, ix[0].z, ix[0].w, ix[1].x, ix[1].y, ix[1].z, ix[1].w,
-                                   ix[2].x, ix[2].y, ix[2].z, ix[2].w, ix[3].x, ix[3].y, ix[3].z, ix[3].w};
+    for (int c = 0; c < 4; ++c)
+      if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
+  }
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const uint32_t bits = (e & 1) ? (hw[e >> 1] >> 16) : (hw[e >> 1] & 0xFFFFu);
-            const bool ok = kw[e] < (uint32_t)NL;               // out-of-range entries are ignored
-            const float t = ok ? __half2float(__ushort_as_half((unsigned short)bits)) : 0.0f;
-            const float* lk = Ls + (long long)(ok ? kw[e] : 0u) * C;
+  for (int c = 0; c < 4; ++c) {
+    float x = acc[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    acc[c] = x;
+  }
+  if (lane == 0) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
-          }
-        }
-      } else {
-        for (int j = lane; j < K; j += 32) {
-          const long long k0 = __ldg(idx + row + j);
-          const bool ok = k0 < NL;
-          const float t = ok ? __half2float(vals[row + j]) : 0.0f;
-          const float* lk = Ls + (ok ? k0 : 0) * C;
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float x = acc[c];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        acc[c] = x;
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c < C) R[((long long)v * S + s) * C + c] = acc[c];
-      }
-    }
+    for (int c = 0; c < 4; ++c)
+      if (c < C) R[((long long)v * S + s) * C + c] = acc[c];
   }
 }
 
 // ---------------------------------------------------------------- vertex-group CSR
-// The top-K sets of neighbouring vertices overlap heavily (8 consecutive
-// torus vertices: ~345 distinct coefficients of 8 x 256), so groups of 8
-// vertices share one sorted union index list with values [nnz_g][8] (zero
-// where a vertex lacks the coefficient): every lighting row loaded feeds 8
-// vertices.  One warp per group: lane = vl + 8 * cg; vertex vl, column block
-// cg (a quarter of the columns, NQ float4 per lane per pass).
-constexpr int kGroup = 8;
+// The top-K sets of neighbouring vertices overlap heavily (4 consecutive
+// torus vertices: ~297 distinct coefficients of 4 x 256), so groups of 4
+// vertices share one sorted union index list with values [nnz_g][4] (zero
+// where a vertex lacks the coefficient): every lighting row loaded feeds 4
+// vertices.
+constexpr int kGroup = 4;
 
-__global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restrict__ vals,
-                                                           const uint16_t* __restrict__ idx,
-                                                           const int32_t* __restrict__ gptr, int V,
-                                                           const float* __restrict__ L, int NL, int ncols,
-                                                           float* __restrict__ R) {
-  // CTA = 4 groups x 2 warps (each warp half of the group's union list).
-  // The union list is streamed in batches of 32 entries: one coalesced load
-  // of 32 indices (kept in a register, broadcast by shuffles) and of their
-  // 32 x 8 values (staged in shared memory), the next batch prefetched into
-  // registers while the current one is consumed.  Lanes 0-15 take even
-  // entries, lanes 16-31 odd ones; lane q of a half owns float4 column chunk
-  // q for all 8 vertices of the group, so each lighting chunk loaded feeds
-  // 32 FMAs.
-  __shared__ float4 red[4][16][kGroup];
-  __shared__ float4 sv[8][32][2];
+// CTA = 4 groups x 2 warps (each warp half of the group's union list, added
+// through shared memory at the end).  A warp takes 8 entries per step: lane
+// = 4 e + cq, entry slot e, column quarter cq (NQ float4 of the lighting
+// row), and accumulates its columns for the 4 vertices of the group; the 8
+// slots are summed with shuffles at the end.  The union list streams in
+// batches of 32 (indices kept in a register, values staged in shared
+// memory), the next batch prefetched while the current one is used.
+template <int NQ>
+__global__ void __launch_bounds__(256) k_shade_gcsr_f32(const float* __restrict__ vals,
+                                                        const uint16_t* __restrict__ idx,
+                                                        const int32_t* __restrict__ gptr, int V,
+                                                        const float* __restrict__ L, int NL, int ncols,
+                                                        float* __restrict__ R) {
+  __shared__ float4 red[4][4][kGroup][NQ];
+  __shared__ float4 sv[8][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gl = w >> 1, wh = w & 1;
   const int g = blockIdx.x * 4 + gl;
   const int n_groups = (V + kGroup - 1) / kGroup;
   const bool active = g < n_groups;
-  const int eh = lane >> 4, q = lane & 15;
+  const int es = lane >> 2, cq = lane & 3;
   int jb = 0, je = 0;
   if (active) {
     const int beg = __ldg(gptr + g), end = __ldg(gptr + g + 1);
@@ -231,73 +200,85 @@ __global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restri
   const int nq = ncols >> 2;
   const float4* L4 = reinterpret_cast<const float4*>(L);
   const float4* V4 = reinterpret_cast<const float4*>(vals);
-  for (int q0 = 0; q0 < nq; q0 += 16) {
-    const int qq = q0 + q;
-    const bool qok = qq < nq;
-    float4 acc[kGroup];
+  for (int q0 = 0; q0 < nq; q0 += 4 * NQ) {
+    const int qb = q0 + cq * NQ;
+    float4 acc[kGroup][NQ];
 #pragma unroll
-    for (int v = 0; v < kGroup; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // prefetch the first batch
+    for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) acc[v][m] = make_float4(0.f, 0.f, 0.f, 0.f);
     int nk = NL;
-    float4 nv0 = make_float4(0.f, 0.f, 0.f, 0.f), nv1 = nv0;
+    float4 nv = make_float4(0.f, 0.f, 0.f, 0.f);
     if (jb + lane < je) {
       nk = __ldg(idx + jb + lane);
-      nv0 = __ldg(V4 + 2 * (jb + lane));
-      nv1 = __ldg(V4 + 2 * (jb + lane) + 1);
+      nv = __ldg(V4 + jb + lane);
     }
     for (int j0 = jb; j0 < je; j0 += 32) {
       const int cnt = min(32, je - j0);
       const int myk = nk;
       __syncwarp();
-      sv[w][lane][0] = nv0;
-      sv[w][lane][1] = nv1;
+      sv[w][lane] = nv;
       __syncwarp();
       const int jn = j0 + 32 + lane;
       nk = NL;
       if (jn < je) {
         nk = __ldg(idx + jn);
-        nv0 = __ldg(V4 + 2 * jn);
-        nv1 = __ldg(V4 + 2 * jn + 1);
+        nv = __ldg(V4 + jn);
       }
-      const int pairs = (cnt + 1) >> 1;                            // same trip count in both halves
-#pragma unroll 4
-      for (int pp = 0; pp < pairs; ++pp) {
-        const int e = 2 * pp + eh;
-        const int k = __shfl_sync(0xffffffffu, myk, e & 31);
-        const bool ok = e < cnt && k < NL && qok;                  // out-of-range entries are ignored
-        const float4 x = ok ? __ldg(L4 + (unsigned)k * (unsigned)nq + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 t0 = sv[w][e & 31][0], t1 = sv[w][e & 31][1];
-        const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
-        for (int v = 0; v < kGroup; ++v) {
-          acc[v].x = fmaf(t[v], x.x, acc[v].x);
-          acc[v].y = fmaf(t[v], x.y, acc[v].y);
-          acc[v].z = fmaf(t[v], x.z, acc[v].z);
-          acc[v].w = fmaf(t[v], x.w, acc[v].w);
+      for (int p = 0; p < 4; ++p) {
+        const int e = 8 * p + es;
+        const int k = __shfl_sync(0xffffffffu, myk, e);
+        const bool ok = e < cnt && k < NL;                      // out-of-range entries are ignored
+        const float4 t = sv[w][e];
+        const float tt[4] = {t.x, t.y, t.z, t.w};
+        float4 x[NQ];
+#pragma unroll
+        for (int m = 0; m < NQ; ++m)
+          x[m] = (ok && qb + m < nq) ? __ldg(L4 + (unsigned)k * (unsigned)nq + qb + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) {
+            acc[v][m].x = fmaf(tt[v], x[m].x, acc[v][m].x);
+            acc[v][m].y = fmaf(tt[v], x[m].y, acc[v][m].y);
+            acc[v][m].z = fmaf(tt[v], x[m].z, acc[v][m].z);
+            acc[v][m].w = fmaf(tt[v], x[m].w, acc[v][m].w);
+          }
+      }
+    }
+    // sum the 8 entry slots (lanes cq, cq + 4, ..., cq + 28)
+#pragma unroll
+    for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+      for (int m = 0; m < NQ; ++m)
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+          acc[v][m].x += __shfl_xor_sync(0xffffffffu, acc[v][m].x, o);
+          acc[v][m].y += __shfl_xor_sync(0xffffffffu, acc[v][m].y, o);
+          acc[v][m].z += __shfl_xor_sync(0xffffffffu, acc[v][m].z, o);
+          acc[v][m].w += __shfl_xor_sync(0xffffffffu, acc[v][m].w, o);
         }
-      }
-    }
-    // odd-entry half into the even half, then the second warp into the first
+    if (wh == 1 && es == 0) {
 #pragma unroll
-    for (int v = 0; v < kGroup; ++v) {
-      acc[v].x += __shfl_down_sync(0xffffffffu, acc[v].x, 16);
-      acc[v].y += __shfl_down_sync(0xffffffffu, acc[v].y, 16);
-      acc[v].z += __shfl_down_sync(0xffffffffu, acc[v].z, 16);
-      acc[v].w += __shfl_down_sync(0xffffffffu, acc[v].w, 16);
-    }
-    if (wh == 1 && eh == 0) {
+      for (int v = 0; v < kGroup; ++v)
 #pragma unroll
-      for (int v = 0; v < kGroup; ++v) red[gl][q][v] = acc[v];
+        for (int m = 0; m < NQ; ++m) red[gl][cq][v][m] = acc[v][m];
     }
     __syncthreads();
-    if (wh == 0 && eh == 0 && active && qok) {
+    if (wh == 0 && es == 0 && active) {
 #pragma unroll
       for (int v = 0; v < kGroup; ++v) {
         const int vv = g * kGroup + v;
         if (vv < V) {
-          const float4 o = red[gl][q][v];
-          reinterpret_cast<float4*>(R + (long long)vv * ncols)[qq] =
-              make_float4(acc[v].x + o.x, acc[v].y + o.y, acc[v].z + o.z, acc[v].w + o.w);
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) {
+            if (qb + m < nq) {
+              const float4 o = red[gl][cq][v][m];
+              reinterpret_cast<float4*>(R + (long long)vv * ncols)[qb + m] =
+                  make_float4(acc[v][m].x + o.x, acc[v][m].y + o.y, acc[v][m].z + o.z, acc[v][m].w + o.w);
+            }
+          }
         }
       }
     }
@@ -474,7 +455,11 @@ haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, cons
                                     const float* L, int NL, int ncols, float* R, cudaStream_t st) {
   const long long groups = (V + kGroup - 1) / kGroup;
   const unsigned nb = (unsigned)((groups + 3) / 4);
-  k_shade_gcsr_f32<<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  const int nq = ncols / 4;
+  if (nq <= 4) k_shade_gcsr_f32<1><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq <= 8) k_shade_gcsr_f32<2><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq <= 12) k_shade_gcsr_f32<3><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else k_shade_gcsr_f32<4><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
   return cuda_check(cudaGetLastError(), "k_shade_gcsr_f32 launch");
 }
 
@@ -496,8 +481,9 @@ haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16
 haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,
                                       int V, int bins, int K, int S, int C, const float* L, long long NL,
                                       float* R, cudaStream_t st) {
-  const unsigned nb = (unsigned)((V + kBinVerts - 1) / kBinVerts);
-  k_shade_bincsr_f16<<<nb, 256, 0, st>>>(vals, idx, bin_of, V, bins, K, S, C, L, NL, R);
+  const long long threads = (long long)V * S * 32;
+  k_shade_bincsr_f16<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(vals, idx, bin_of, V, bins, K, S, C, L,
+                                                                        NL, R);
   return cuda_check(cudaGetLastError(), "k_shade_bincsr_f16 launch");
 }
 

@@ -377,6 +377,44 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   if (threadIdx.x == 0) a.counters[s] = 0u;
 }
 
+// Morton (Z-order) coordinates: x from the even bits, y from the odd bits.
+__device__ __forceinline__ int morton_x(int t) {
+  return (t & 1) | ((t >> 1) & 2) | ((t >> 2) & 4) | ((t >> 3) & 8) | ((t >> 4) & 16);
+}
+__device__ __forceinline__ int morton_y(int t) { return morton_x(t >> 1); }
+
+// One level of the transform on 4 values held by Morton-consecutive lane
+// groups (lanes base + {0, st, 2 st, 3 st} = top-left, top-right,
+// bottom-left, bottom-right): every lane gets the merged scaling value; the
+// first three members write the H, V and D coefficient of block
+// (by >> (lvl - 2), bx >> (lvl - 2)) of the tile at level lvl, where (by, bx)
+// is the lane's 4 x 4 block; only lanes below `limit` write.  All 32 lanes
+// must call it.
+template <int OUT>
+__device__ __forceinline__ float merge4(const ShiftArgs& a, const ShiftParam* p, int s, int c, float A, int lane,
+                                        int st, int lvl, int i0, int j0, int by, int bx, int limit = 32) {
+  const int base = lane & ~(4 * st - 1);
+  const float e0 = __shfl_sync(0xffffffffu, A, base);
+  const float e1 = __shfl_sync(0xffffffffu, A, base + st);
+  const float e2 = __shfl_sync(0xffffffffu, A, base + 2 * st);
+  const float e3 = __shfl_sync(0xffffffffu, A, base + 3 * st);
+  const int m = (lane - base) / st;
+  if ((lane & (st - 1)) == 0 && m < 3 && lane < limit) {
+    const float d = (m == 0) ? 0.5f * ((e1 + e3) - (e0 + e2))
+                  : (m == 1) ? 0.5f * ((e2 + e3) - (e0 + e1)) : 0.5f * ((e0 + e3) - (e1 + e2));
+    const Geometry& g = a.g;
+    const int gl = g.q << (2 * (g.n - lvl));
+    const int r = (i0 >> lvl) + (by >> (lvl - 2)), col = (j0 >> lvl) + (bx >> (lvl - 2));
+    const int k = gl * (1 + m) + r * (g.W >> lvl) + col;
+    if (k < a.K) {
+      float v = d;
+      if (p != nullptr && ((p->perm_mask >> lvl) & 1u)) v = perm_value(a, *p, c, lvl, m, r, col);
+      store_at<OUT>(a, (long long)s * a.st_s + (long long)c * a.st_c + (long long)k * a.st_k, v);
+    }
+  }
+  return 0.5f * ((e0 + e1) + (e2 + e3));
+}
+
 // Register path for 32 x 32 and 64 x 64 tiles: every thread resamples its own
 // 4 x 4 block of output pixels straight from the L2-resident pixel map
 // (translation: the 5 x 5 source window, all 25 loads in flight; rotation:
@@ -399,12 +437,12 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
   if (KIND != KIND_COPY && threadIdx.x == 0) s_prm = a.prm[s];
   __syncthreads();
   const ShiftParam* p = (KIND == KIND_COPY) ? nullptr : &s_prm;
-  const int lnb = g.Lt - 2;                         // nb = 2^lnb
-  const int by = threadIdx.x >> lnb, bx = threadIdx.x & (nb - 1);
+  // Morton (Z-order) placement of the thread's 4 x 4 block: the 4, 16, 64 ...
+  // blocks that merge at levels 3, 4, 5 ... are consecutive threads
+  const int by = morton_y(threadIdx.x), bx = morton_x(threadIdx.x);
   const int i0 = tr * T + 4 * by, j0 = tc * T + 4 * bx;
   const int Wm = g.W - 1;
   float* sA = smem;                                 // [CG][nb * nb]
-  float* sB = smem + CG * nb * nb;                  // pass scratch (nb/4)^2
 
   float x[CG][16];
   if (KIND == KIND_TRANSLATE) {
@@ -506,6 +544,7 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
   const int g1 = g.q << (2 * (g.n - 1)), g2 = g.q << (2 * (g.n - 2));
   const bool fast = OUT == HAAR_OUT_F32 && a.st_k == 1 && a.scale == 1.0f && (p == nullptr || p->perm_mask == 0u) &&
                     4 * g1 <= a.K && g.n >= 2;
+  float a2[CG];
 #pragma unroll
   for (int ci = 0; ci < CG; ++ci) {
     if (ci >= cgn) continue;
@@ -539,36 +578,54 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
         p2[2 * g2] = 0.5f * ((ec + ed) - (ea + eb));
         p2[3 * g2] = 0.5f * ((ea + ed) - (eb + ec));
       }
-      sA[ci * nb * nb + threadIdx.x] = 0.5f * ((ea + eb) + (ec + ed));
+      a2[ci] = 0.5f * ((ea + eb) + (ec + ed));
     } else {
-      sA[ci * nb * nb + threadIdx.x] = block4<OUT>(a, p, s, c0 + ci, x[ci], 0, tr * T, tc * T, by, bx);
+      a2[ci] = block4<OUT>(a, p, s, c0 + ci, x[ci], 0, tr * T, tc * T, by, bx);
     }
   }
 
+  // levels 3..Lt: merges of 4 Morton-consecutive values, first inside each
+  // warp (shuffles, lanes in groups of 4 then 16), then one warp finishes the
+  // tile from the per-group values left in shared memory
+  const int lane = threadIdx.x & 31;
+  const int nthreads = nb * nb;
   for (int ci = 0; ci < cgn; ++ci) {
     const int c = c0 + ci;
-    // levels 3..Lt on the nb x nb scaling image
-    int side = nb, lvl = 2;
-    float* src = sA + ci * nb * nb;
-    float* dst = sB;
-    while (lvl < g.Lt) {
-      const int sb = (g.Lt - lvl >= 2) ? 4 : 2;
-      __syncthreads();
-      haar_pass<OUT>(a, p, s, c, src, dst, side, side, lvl, sb, (tr * T) >> lvl, (tc * T) >> lvl);
-      side /= sb;
-      lvl += (sb == 4) ? 2 : 1;
-      float* t = src; src = dst; dst = t;
+    float A = a2[ci];
+    int lvl = 2;
+    int st = 1;                                     // lane stride between the 4 merged values
+#pragma unroll
+    for (int step = 0; step < 2; ++step) {
+      if (lvl >= g.Lt || 4 * st > nthreads || 4 * st > 32) break;
+      A = merge4<OUT>(a, p, s, c, A, lane, st, lvl + 1, tr * T, tc * T, by, bx);
+      ++lvl;
+      st *= 4;
     }
+    // one value per group of st threads remains
+    const int groups = nthreads / st;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const float m = src[0];
-      if (a.means != nullptr)
-        a.means[((long long)s * g.C + c) * g.n_tiles + tile] = m;
-      else
-        reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = m;
+    if ((threadIdx.x & (st - 1)) == 0) sA[threadIdx.x / st] = A;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // the remaining levels on `groups` values (a Morton-ordered grid of blocks of side 2^lvl)
+      float B = (lane < groups) ? sA[lane] : 0.0f;
+      const int l1 = lvl;                         // group lane = Morton index of a level-l1 block
+      const int gy = morton_y(lane) << (l1 - 2), gx = morton_x(lane) << (l1 - 2);
+      int st2 = 1;
+      while (lvl < g.Lt) {
+        B = merge4<OUT>(a, p, s, c, B, lane, st2, lvl + 1, tr * T, tc * T, gy, gx, groups);
+        ++lvl;
+        st2 *= 4;
+      }
+      if (lane == 0) {
+        if (a.means != nullptr)
+          a.means[((long long)s * g.C + c) * g.n_tiles + tile] = B;
+        else
+          reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = B;
+      }
     }
-    __syncthreads();
   }
+  __syncthreads();
 
   if (a.counters == nullptr) return;
   if (threadIdx.x == 0) {

@@ -169,6 +169,15 @@ def test_fused_shade_matches_oracle(hs):
         ref[:, s] = om.shade_from_outputs(out, mu, sg, Ls[s][:, idx])
     assert rel_l2(R, ref) <= FWD_TOL
     net.close()
+    # the layer-by-layer path (taken when the per-vertex table does not fit the
+    # inference buffers) gives the same result within bf16 storage
+    small = hs.Surrogate(max_batch=128, max_rows=128, max_groups=S)
+    small.set_params(_t(_flat(P), None).float())
+    R2 = small.shade(_t(pos).float(), _t(nrm).float(), _t(cams).float(), _t(mu).float(), _t(sg).float(),
+                     _t(idx, torch.int32), _t(Ls).float(), C, (C * H * W, H * W, 1)).cpu().numpy()
+    assert rel_l2(R2, ref) <= FWD_TOL
+    assert rel_l2(R2, R) <= FWD_TOL
+    small.close()
 
 
 def _glossy_dataset(n, seed, device="cuda", chunk=8192):

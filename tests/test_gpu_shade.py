@@ -115,7 +115,7 @@ def test_csr_ragged_rows(hs):
     assert rel_l2(got, ref) <= 1e-5
 
 
-def _group_reference(vals, idx, rowptr, V, G=8):
+def _group_reference(vals, idx, rowptr, V, G=4):
     """Union index list and [nnz][G] values of every group of G rows."""
     gptr, gidx, gvals = [0], [], []
     for g0 in range(0, V, G):
@@ -169,7 +169,7 @@ def test_csr_full_size_c1_sampled(hs):
     ref = osd.radiance(Ls, dense, H, W)
     assert rel_l2(got[pick], ref) <= 1e-5
     assert np.isfinite(got).all()
-    # the same frame through the 8-vertex group CSR the bench times
+    # the same frame through the 4-vertex group CSR the bench times
     import torch
     trg = hs.haar_transport_group(sc["V"], H * W, _t(rowptr.astype(np.int32), torch.int32),
                                   _t(idx.astype(np.int16), torch.int16), _t(vals, torch.float32))

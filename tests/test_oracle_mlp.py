@@ -55,12 +55,17 @@ def test_encoding_layout():
     e = mlp.encode(raw)
     assert e.shape == (1, 320)
     assert mlp.N_ENC == 297
-    assert np.all(e[0, 297:] == 0.0)
-    assert np.allclose(e[0, :9], raw[0])
+    assert np.count_nonzero(e[0, 299:]) == 0 and np.all(e[0, 198:200] == 0.0)
+    assert np.allclose(e[0, :6], raw[0, :6]) and np.allclose(e[0, 200:203], raw[0, 6:])
     w3 = math.pi * 2 ** 1.5
-    o = 9 + 18 * 3
-    assert np.allclose(e[0, o:o + 9], np.sin(w3 * raw[0]))
-    assert np.allclose(e[0, o + 9:o + 18], np.cos(w3 * raw[0]))
+    assert np.allclose(e[0, 6 + 36:12 + 36], np.sin(w3 * raw[0, :6]))
+    assert np.allclose(e[0, 12 + 36:18 + 36], np.cos(w3 * raw[0, :6]))
+    assert np.allclose(e[0, 203 + 18:206 + 18], np.sin(w3 * raw[0, 6:]))
+    assert np.allclose(e[0, 206 + 18:209 + 18], np.cos(w3 * raw[0, 6:]))
+    # the first 200 columns depend on position and normal only
+    raw2 = raw.copy()
+    raw2[0, 6:] = [0.3, -0.2, 0.9]
+    assert np.array_equal(mlp.encode(raw2)[0, :200], e[0, :200])
 
 
 def test_adam_first_step_moves_by_lr_times_sign():
