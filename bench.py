@@ -300,6 +300,7 @@ def measure_rows(hs, dev, flush, only=None):
                                         device=dev, dtype=torch.float32, chunk=8192).contiguous()
             T[a:b] = hs.haar_forward(w, scale=0.25)[:, :K].to(torch.bfloat16)
             del w
+        L2 = hs.haar_forward(torch.tensor(sc2["light"], dtype=torch.float32, device=dev))
         eul = torch.tensor(sc2["params"], dtype=torch.float64, device=dev)
         plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_coeffs=K,
                        out_type=hs.HAAR_OUT_BF16_HILO)
