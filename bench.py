@@ -182,8 +182,9 @@ def algorithmic_bytes(wl):
     """Bytes a kernel must move at least, per launch: its stored input read
     once, the lighting read once, its output written once."""
     V, K, S, C, N = wl["V"], wl["K"], wl["S"], wl["C"], wl["H"] * wl["W"]
-    U, G = wl["union"], (wl["V"] + 3) // 4
-    gcsr = U * (4 * 4 + 2) + (G + 1) * 4 + N * S * C * 4 + V * S * C * 4
+    import paper_1705_07272_gb300 as hs
+    U, G = wl["union"], (wl["V"] + hs.GROUP - 1) // hs.GROUP
+    gcsr = U * (4 * hs.GROUP + 2) + (G + 1) * 4 + N * S * C * 4 + V * S * C * 4
     csr = V * K * 4 + V * K * 2 + (V + 1) * 4 + N * S * C * 4 + V * S * C * 4
     shift = C * N * 4 + S * C * N * 4
     return {"k_shade_gcsr_f32": gcsr, "k_shade_csr_f32": csr, "k_shift": shift}

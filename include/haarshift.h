@@ -111,6 +111,13 @@ HAAR_API haar_status_t haar_shift_plan(const haar_shift_desc_t* desc, haar_shift
 /* Release a plan and its workspace (synchronises the device first). */
 HAAR_API haar_status_t haar_shift_plan_destroy(haar_shift_plan_t plan);
 
+/* Device-side status of the plan's kernels since the last reset: bit
+ * (1 << HAAR_ERR_TIMEOUT) is set when a bounded wait of a pipelined kernel
+ * (tensor-core contraction, group-CSR shading) gave up; that launch's
+ * radiance is then incomplete.  Synchronises the device; *status_out
+ * receives the bits (0 = fine); reset != 0 clears them. */
+HAAR_API haar_status_t haar_shift_plan_status(haar_shift_plan_t plan, int* status_out, int reset);
+
 /* The phase shift (Sec. "Rotating Haar" and "Mathematical description";
  * Sec. "Algorithmic optimization" for the O(N) cost):
  *   coeffs_out[s] = Haar( resample_s( Haar^-1(coeffs_in) ) ),  s = 0..S-1.
@@ -168,11 +175,15 @@ typedef enum {
   HAAR_T_BINCSR_F16_U32 = 3, /* vals [V][bins][K] binary16, idx [V][bins][K] uint32,
                                bin_of [S][V] uint8 selects the bin of (s, v) */
   HAAR_T_GCSR_F32_U16 = 4    /* vertex-group CSR made by haar_transport_group: groups of
-                               4 consecutive vertices share one sorted union index list
-                               idx (uint16) with values [nnz][4] float32 (0 where a
-                               vertex lacks the coefficient); rowptr = group offsets
-                               [ceil(V/4) + 1] int32 */
+                               HAAR_GCSR_GROUP consecutive vertices share one sorted
+                               union index list idx (uint16) with values
+                               [nnz][HAAR_GCSR_GROUP] float32 (0 where a vertex lacks
+                               the coefficient); rowptr = group offsets
+                               [ceil(V/HAAR_GCSR_GROUP) + 1] int32 */
 } haar_transport_kind_t;
+
+/* vertices per group of HAAR_T_GCSR_F32_U16 */
+#define HAAR_GCSR_GROUP 4
 
 typedef struct {
   int kind;                    /* haar_transport_kind_t */
@@ -196,7 +207,9 @@ typedef struct {
  *   CSR_F32_U16      with F32  lighting, layout KSC (S*C % 4 == 0);
  *   BINCSR_F16_U32   with F32  lighting, layout SKC;
  *   GCSR_F32_U16     with F32  lighting, layout KSC (S*C % 4 == 0).
- * radiance: [V][S][C] float32, overwritten. */
+ * radiance: [V][S][C] float32, overwritten.  Launches that use the same plan
+ * must be ordered (one stream, or events): the plan's workspace and device
+ * counters are shared. */
 HAAR_API haar_status_t shade_vertices(haar_shift_plan_t plan, const haar_transport_desc_t* transport,
                              const void* lighting, int S, float* radiance, void* stream);
 
@@ -208,14 +221,15 @@ HAAR_API haar_status_t shade_batch(haar_shift_plan_t plan, const float* coeffs_i
 
 /* Repack top-K CSR transport (rows sorted by index, rowptr int32 [V+1],
  * idx uint16, vals float32) into the vertex-group CSR of HAAR_T_GCSR_F32_U16:
- * the union of the indices of every 4 consecutive rows, sorted, with the
- * values of each row at its union positions (0 elsewhere).  A storage form
- * of the top-K (non-linear) approximation cited in Sec. "Haar-domain
- * methods": the double product is unchanged, each lighting row gathered
- * serves 4 vertices.  N: coefficients per map (<= 65536; indices >= N are
- * dropped).  gptr [ceil(V/4) + 1] int32 (device) receives the group offsets;
- * gptr[ceil(V/4)] is the total.  Call once with gidx = gvals = NULL to get
- * gptr, then again with gidx [total] uint16 and gvals [total][4] float32. */
+ * the union of the indices of every HAAR_GCSR_GROUP (G) consecutive rows,
+ * sorted, with the values of each row at its union positions (0 elsewhere).
+ * A storage form of the top-K (non-linear) approximation cited in Sec.
+ * "Haar-domain methods": the double product is unchanged, each lighting row
+ * gathered serves G vertices.  N: coefficients per map (<= 65536; indices
+ * >= N are dropped).  gptr [ceil(V/G) + 1] int32 (device) receives the group
+ * offsets; gptr[ceil(V/G)] is the total.  Call once with gidx = gvals = NULL
+ * to get gptr, then again with gidx [total] uint16 and gvals [total][G]
+ * float32 (16-byte aligned). */
 HAAR_API haar_status_t haar_transport_group(int V, int N, const int32_t* rowptr, const uint16_t* idx,
                                             const float* vals, int32_t* gptr, uint16_t* gidx, float* gvals,
                                             void* stream);

@@ -44,14 +44,14 @@ HAAR_T_DENSE_BF16 = 1
 HAAR_T_CSR_F32_U16 = 2
 HAAR_T_BINCSR_F16_U32 = 3
 HAAR_T_GCSR_F32_U16 = 4
-GROUP = 4            # vertices per group of HAAR_T_GCSR_F32_U16
+GROUP = 4            # vertices per group of HAAR_T_GCSR_F32_U16 (HAAR_GCSR_GROUP)
 
 EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_forward",
            "haar_inverse", "shade_vertices", "shade_batch", "haar_view_bins",
            "haar_last_error", "haar_version", "haar_mlp_param_count", "haar_mlp_create",
            "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params", "haar_mlp_forward",
            "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status",
-           "haar_shift_noalloc", "haar_transport_group")
+           "haar_shift_noalloc", "haar_transport_group", "haar_shift_plan_status")
 
 
 class HaarShiftDesc(ctypes.Structure):
@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
     L.haar_view_bins.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp]
     L.haar_transport_group.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp]
     L.haar_transport_group.restype = st
+    L.haar_shift_plan_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i]
+    L.haar_shift_plan_status.restype = st
     for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_shift_noalloc", "haar_forward", "haar_inverse",
                  "shade_vertices", "shade_batch", "haar_view_bins"):
         getattr(L, name).restype = st
@@ -182,6 +184,13 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def status(self, reset=False):
+        """Device status bits of the plan's kernels (0 = fine; bit 1 << 4: a
+        bounded wait gave up).  Synchronises the device."""
+        v = ctypes.c_int(0)
+        _check(lib().haar_shift_plan_status(self.handle, ctypes.byref(v), 1 if reset else 0))
+        return v.value
 
     def out_shape(self, S):
         """Shape of haar_shift's output tensor for S shifts."""

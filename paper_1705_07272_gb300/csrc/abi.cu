@@ -114,7 +114,10 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
   if (e == cudaSuccess) e = cudaMalloc(&p->pix, sizeof(float) * g.N * g.C);
   if (e == cudaSuccess) e = cudaMalloc(&p->trig, sizeof(float) * 2 * (g.H + g.W));
   if (e == cudaSuccess) e = cudaMalloc(&p->prm, sizeof(ShiftParam) * S);
-  if (e == cudaSuccess) e = cudaMalloc(&p->means, sizeof(float) * S * g.C * g.n_tiles);
+  p->means_cap = S * g.C * g.n_tiles;
+  if (ksc_eligible(*d, (int)S) && ksc_means_floats(*d, (int)S) > p->means_cap)
+    p->means_cap = ksc_means_floats(*d, (int)S);
+  if (e == cudaSuccess) e = cudaMalloc(&p->means, sizeof(float) * p->means_cap);
   if (e == cudaSuccess) e = cudaMalloc(&p->counters, sizeof(unsigned) * S);
   if (e == cudaSuccess) e = cudaMalloc(&p->light, light_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int) * 4);
@@ -144,6 +147,15 @@ haar_status_t haar_shift_plan_destroy(haar_shift_plan_t p) {
   cudaError_t e = cudaDeviceSynchronize();
   free_plan(p);
   return cuda_check(e, "haar_shift_plan_destroy: synchronise");
+}
+
+haar_status_t haar_shift_plan_status(haar_shift_plan_t p, int* status_out, int reset) {
+  HS_ENTRY("haar_shift_plan_status");
+  if (p == nullptr || status_out == nullptr) return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan_status: null argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status_out, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(p->status, 0, sizeof(int));
+  return cuda_check(e, "haar_shift_plan_status");
 }
 
 static haar_status_t check_shift_args(haar_shift_plan_t p, const float* cin, const double* params, int S,
@@ -237,11 +249,11 @@ static haar_status_t shade_impl(haar_shift_plan_t p, const haar_transport_desc_t
         return set_error(HAAR_ERR_UNSUPPORTED, "%s: GCSR_F32_U16 needs F32 lighting in KSC layout", who);
       if (ncols % 4 != 0) return set_error(HAAR_ERR_UNSUPPORTED, "%s: GCSR needs S*C %% 4 == 0", who);
       if (t->idx == nullptr || t->rowptr == nullptr) return set_error(HAAR_ERR_INVALID_ARG, "%s: GCSR needs idx and rowptr", who);
-      if (!aligned(L, 16) || !aligned(R, 16))
-        return set_error(HAAR_ERR_INVALID_ARG, "%s: lighting and radiance must be 16-byte aligned", who);
+      if (!aligned(L, 16) || !aligned(R, 16) || !aligned(t->vals, 16))
+        return set_error(HAAR_ERR_INVALID_ARG, "%s: group values, lighting and radiance must be 16-byte aligned", who);
       if (p->K > 65536) return set_error(HAAR_ERR_UNSUPPORTED, "%s: uint16 indices cover at most 65536 coefficients", who);
       return launch_shade_gcsr_f32((const float*)t->vals, (const uint16_t*)t->idx, t->rowptr, t->V, (const float*)L,
-                                   p->K, ncols, R, st);
+                                   p->K, ncols, R, p->status, st);
     case HAAR_T_BINCSR_F16_U32:
       if (ot != HAAR_OUT_F32 || lay != HAAR_LAYOUT_SKC)
         return set_error(HAAR_ERR_UNSUPPORTED, "%s: BINCSR_F16_U32 needs F32 lighting in SKC layout", who);

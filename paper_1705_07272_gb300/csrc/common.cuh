@@ -69,7 +69,8 @@ struct haar_shift_plan_s {
   float* pix;                // [C][H][W] pixel map synthesised per launch
   float* trig;               // sin_t[H] cos_t[H] sin_p[W] cos_p[W]
   hs::ShiftParam* prm;       // [max_shifts]
-  float* means;              // [max_shifts][C][n_tiles]
+  float* means;              // [max_shifts][C][n_tiles] (or [max_shifts][C][H W / 256] for the KSC kernel)
+  size_t means_cap;          // floats in means
   unsigned* counters;        // [max_shifts]
   void* light;               // shade_batch lighting [max_shifts * C * K] (x2 planes for BF16_HILO)
   size_t light_elems;        // elements per plane
@@ -89,6 +90,9 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
                            cudaStream_t st);
 haar_status_t launch_trig(haar_shift_plan_s* p, cudaStream_t st);
+bool ksc_eligible(const haar_shift_desc_t& d, int S);
+size_t ksc_means_floats(const haar_shift_desc_t& d, int S);
+size_t ksc_smem_floats(long long n16);
 haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* coeffs,
                              float scale, cudaStream_t st);
 haar_status_t launch_inverse(int H, int W, int batch, const float* coeffs, float* maps,
@@ -103,7 +107,7 @@ haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, c
                                       int V, int bins, int K, int S, int C, const float* L,
                                       long long NL, float* R, cudaStream_t st);
 haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, const int32_t* gptr, int V,
-                                    const float* L, int NL, int ncols, float* R, cudaStream_t st);
+                                    const float* L, int NL, int ncols, float* R, int* status, cudaStream_t st);
 haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16_t* idx, const float* vals,
                                int32_t* gptr, uint16_t* gidx, float* gvals, cudaStream_t st);
 haar_status_t launch_view_bins(int V, int S, int bins, const float* pos, const float* nrm,

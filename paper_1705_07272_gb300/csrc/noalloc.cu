@@ -59,7 +59,8 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   const size_t n_pix = round64((size_t)C * N);
   const size_t n_trig = round64(2 * (size_t)(H + W));
   const size_t n_prm = round64((size_t)S * sizeof(ShiftParam) / sizeof(float));
-  const size_t n_means = round64((size_t)S * C * g.n_tiles);
+  size_t n_means = round64((size_t)S * C * g.n_tiles);
+  if (ksc_eligible(*d, S) && round64(ksc_means_floats(*d, S)) > n_means) n_means = round64(ksc_means_floats(*d, S));
   const size_t n_cnt = round64((size_t)S);
   const size_t need = n_pix + n_trig + n_prm + n_means + n_cnt;
   if (need > kNoAllocFloats)
@@ -95,6 +96,7 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   p.trig = base + n_pix;
   p.prm = reinterpret_cast<ShiftParam*>(base + n_pix + n_trig);
   p.means = base + n_pix + n_trig + n_prm;
+  p.means_cap = n_means;
   p.counters = reinterpret_cast<unsigned*>(base + n_pix + n_trig + n_prm + n_means);
   cudaStream_t st = (cudaStream_t)stream;
   haar_status_t r = HAAR_OK;

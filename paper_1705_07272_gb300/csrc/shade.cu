@@ -8,6 +8,7 @@
 // vectors: radiance[v][s][c] = sum_k T[v][k] L'[s][c][k].  Top-K storage is
 // the non-linear wavelet approximation cited in Sec. "Haar-domain methods".
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace hs {
 
@@ -163,126 +164,196 @@ __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restri
 
 // ---------------------------------------------------------------- vertex-group CSR
 // The top-K sets of neighbouring vertices overlap heavily (4 consecutive
-// torus vertices: ~297 distinct coefficients of 4 x 256), so groups of 4
-// vertices share one sorted union index list with values [nnz_g][4] (zero
-// where a vertex lacks the coefficient): every lighting row loaded feeds 4
-// vertices.
-constexpr int kGroup = 4;
+// torus vertices of the 50 000-vertex top-256 scene: ~295 distinct
+// coefficients of 4 x 256), so groups of 4 vertices share one sorted union
+// index list with values [nnz_g][4] (zero where a vertex lacks the
+// coefficient): every lighting row gathered feeds 4 vertices.  (Larger
+// groups cut the row gathers further but lose the L1 reuse of the coarse
+// rows that every group repeats; 4 measured best.)
+constexpr int kGroup = HAAR_GCSR_GROUP;
+static_assert(kGroup == 4, "lane layout below assumes 4-vertex groups");
 
-// CTA = 4 groups x 2 warps (each warp half of the group's union list, added
-// through shared memory at the end).  A warp takes 8 entries per step: lane
+// Paired FP32 arithmetic of sm_100+ (fma.rn.f32x2): two lanes of a 64-bit
+// register pair per instruction, each rounded like fmaf.
+__device__ __forceinline__ unsigned long long f2_dup(float a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_shfl_xor(unsigned long long a, int o) {
+  return __shfl_xor_sync(0xffffffffu, a, o);
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void l2_prefetch_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// 16 bytes that are used once: past L1, so that L1 keeps the lighting rows
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p) {
+  float4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// CTA = 4 groups x 2 warps (a pair per group; the two warps split the
+// group's union list in halves and add through shared memory, a named
+// barrier per pair).  A warp takes 8 entries per step: lane
 // = 4 e + cq, entry slot e, column quarter cq (NQ float4 of the lighting
-// row), and accumulates its columns for the 4 vertices of the group; the 8
-// slots are summed with shuffles at the end.  The union list streams in
-// batches of 32 (indices kept in a register, values staged in shared
-// memory), the next batch prefetched while the current one is used.
-template <int NQ>
-__global__ void __launch_bounds__(256) k_shade_gcsr_f32(const float* __restrict__ vals,
-                                                        const uint16_t* __restrict__ idx,
-                                                        const int32_t* __restrict__ gptr, int V,
-                                                        const float* __restrict__ L, int NL, int ncols,
-                                                        float* __restrict__ R) {
-  __shared__ float4 red[4][4][kGroup][NQ];
+// row), and accumulates its columns for the 4 vertices with paired FMAs;
+// the 8 slots are summed with shuffles at the end.  The union list streams
+// in batches of 32 (indices kept in a register, values staged in shared
+// memory), the next batch requested while the current one is used, the
+// lighting row of step p + 1 in flight while step p's products issue, and
+// the whole half-list sent towards L2 by one bulk prefetch when the group
+// starts; the values are read past L1 (no-allocate), which keeps L1 for the
+// lighting rows.  Entries past the list's end or with an index >= NL become
+// (row 0, value 0), so the inner loop carries no predicate.  EXACT: the row
+// is exactly 4 NQ float4 wide (one column pass, no column guards).
+template <int NQ, bool EXACT>
+__global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restrict__ vals,
+                                                           const uint16_t* __restrict__ idx,
+                                                           const int32_t* __restrict__ gptr, int V,
+                                                           const float* __restrict__ L, int NL, int ncols,
+                                                           float* __restrict__ R) {
+  typedef unsigned long long u64;
+  __shared__ ulonglong2 red[4][4][kGroup][NQ];
   __shared__ float4 sv[8][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gl = w >> 1, wh = w & 1;
-  const int g = blockIdx.x * 4 + gl;
   const int n_groups = (V + kGroup - 1) / kGroup;
-  const bool active = g < n_groups;
   const int es = lane >> 2, cq = lane & 3;
-  int jb = 0, je = 0;
-  if (active) {
+  const int nq = EXACT ? 4 * NQ : (ncols >> 2);
+  const float4* V4 = reinterpret_cast<const float4*>(vals);
+  const int g = blockIdx.x * 4 + gl;
+  if (g < n_groups) {
     const int beg = __ldg(gptr + g), end = __ldg(gptr + g + 1);
     const int mid = beg + (end - beg + 1) / 2;
-    jb = wh ? mid : beg;
-    je = wh ? end : mid;
-  }
-  const int nq = ncols >> 2;
-  const float4* L4 = reinterpret_cast<const float4*>(L);
-  const float4* V4 = reinterpret_cast<const float4*>(vals);
-  for (int q0 = 0; q0 < nq; q0 += 4 * NQ) {
-    const int qb = q0 + cq * NQ;
-    float4 acc[kGroup][NQ];
-#pragma unroll
-    for (int v = 0; v < kGroup; ++v)
-#pragma unroll
-      for (int m = 0; m < NQ; ++m) acc[v][m] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int nk = NL;
-    float4 nv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (jb + lane < je) {
-      nk = __ldg(idx + jb + lane);
-      nv = __ldg(V4 + jb + lane);
+    const int jb = wh ? mid : beg;
+    const int je = wh ? end : mid;
+    if (lane == 0 && je > jb) {
+      l2_prefetch_bulk(vals + 4ll * jb, 16u * (unsigned)(je - jb));
+      const uintptr_t ib = reinterpret_cast<uintptr_t>(idx + jb) & ~uintptr_t(15);
+      const uintptr_t ie = reinterpret_cast<uintptr_t>(idx + je) & ~uintptr_t(15);
+      if (ie > ib) l2_prefetch_bulk(reinterpret_cast<const void*>(ib), (unsigned)(ie - ib));
     }
-    for (int j0 = jb; j0 < je; j0 += 32) {
-      const int cnt = min(32, je - j0);
-      const int myk = nk;
-      __syncwarp();
-      sv[w][lane] = nv;
-      __syncwarp();
-      const int jn = j0 + 32 + lane;
-      nk = NL;
-      if (jn < je) {
-        nk = __ldg(idx + jn);
-        nv = __ldg(V4 + jn);
-      }
+    for (int q0 = 0; q0 < nq; q0 += 4 * NQ) {
+      const int qb = q0 + cq * NQ;
+      // columns beyond the row (generic widths only) read row 0's first float4 and are not stored
+      int qoff[NQ];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int e = 8 * p + es;
-        const int k = __shfl_sync(0xffffffffu, myk, e);
-        const bool ok = e < cnt && k < NL;                      // out-of-range entries are ignored
-        const float4 t = sv[w][e];
-        const float tt[4] = {t.x, t.y, t.z, t.w};
-        float4 x[NQ];
-#pragma unroll
-        for (int m = 0; m < NQ; ++m)
-          x[m] = (ok && qb + m < nq) ? __ldg(L4 + (unsigned)k * (unsigned)nq + qb + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int v = 0; v < kGroup; ++v)
-#pragma unroll
-          for (int m = 0; m < NQ; ++m) {
-            acc[v][m].x = fmaf(tt[v], x[m].x, acc[v][m].x);
-            acc[v][m].y = fmaf(tt[v], x[m].y, acc[v][m].y);
-            acc[v][m].z = fmaf(tt[v], x[m].z, acc[v][m].z);
-            acc[v][m].w = fmaf(tt[v], x[m].w, acc[v][m].w);
-          }
-      }
-    }
-    // sum the 8 entry slots (lanes cq, cq + 4, ..., cq + 28)
-#pragma unroll
-    for (int v = 0; v < kGroup; ++v)
-#pragma unroll
-      for (int m = 0; m < NQ; ++m)
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-          acc[v][m].x += __shfl_xor_sync(0xffffffffu, acc[v][m].x, o);
-          acc[v][m].y += __shfl_xor_sync(0xffffffffu, acc[v][m].y, o);
-          acc[v][m].z += __shfl_xor_sync(0xffffffffu, acc[v][m].z, o);
-          acc[v][m].w += __shfl_xor_sync(0xffffffffu, acc[v][m].w, o);
-        }
-    if (wh == 1 && es == 0) {
+      for (int m = 0; m < NQ; ++m) qoff[m] = (EXACT || qb + m < nq) ? qb + m : 0;
+      u64 acc[kGroup][NQ][2];
 #pragma unroll
       for (int v = 0; v < kGroup; ++v)
 #pragma unroll
-        for (int m = 0; m < NQ; ++m) red[gl][cq][v][m] = acc[v][m];
-    }
-    __syncthreads();
-    if (wh == 0 && es == 0 && active) {
+        for (int m = 0; m < NQ; ++m) acc[v][m][0] = acc[v][m][1] = 0ull;
+      int nk = 0;
+      float4 nv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (jb + lane < je) {
+        nk = __ldg(idx + jb + lane);
+        nv = ld_stream_f4(V4 + jb + lane);
+        if (nk >= NL) { nk = 0; nv = make_float4(0.f, 0.f, 0.f, 0.f); }
+      }
+      for (int j0 = jb; j0 < je; j0 += 32) {
+        const int myk = nk;
+        __syncwarp();
+        sv[w][lane] = nv;
+        __syncwarp();
+        const int jn = j0 + 32 + lane;
+        nk = 0;
+        nv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jn < je) {
+          nk = __ldg(idx + jn);
+          nv = ld_stream_f4(V4 + jn);
+          if (nk >= NL) { nk = 0; nv = make_float4(0.f, 0.f, 0.f, 0.f); }
+        }
+        const int steps = min(4, (je - j0 + 7) >> 3);           // warp-uniform
+        // software pipeline: the lighting row of step p + 1 is in flight while
+        // step p's products issue
+        ulonglong2 x[NQ];
+        {
+          const int k = __shfl_sync(0xffffffffu, myk, es);
+          const ulonglong2* row = reinterpret_cast<const ulonglong2*>(L) + (unsigned)k * (unsigned)nq;
 #pragma unroll
-      for (int v = 0; v < kGroup; ++v) {
-        const int vv = g * kGroup + v;
-        if (vv < V) {
+          for (int m = 0; m < NQ; ++m) x[m] = __ldg(row + qoff[m]);
+        }
 #pragma unroll
-          for (int m = 0; m < NQ; ++m) {
-            if (qb + m < nq) {
-              const float4 o = red[gl][cq][v][m];
-              reinterpret_cast<float4*>(R + (long long)vv * ncols)[qb + m] =
-                  make_float4(acc[v][m].x + o.x, acc[v][m].y + o.y, acc[v][m].z + o.z, acc[v][m].w + o.w);
+        for (int p = 0; p < 4; ++p) {
+          if (p < steps) {
+            ulonglong2 xn[NQ];
+            if (p + 1 < steps) {
+              const int k = __shfl_sync(0xffffffffu, myk, 8 * (p + 1) + es);
+              const ulonglong2* row = reinterpret_cast<const ulonglong2*>(L) + (unsigned)k * (unsigned)nq;
+#pragma unroll
+              for (int m = 0; m < NQ; ++m) xn[m] = __ldg(row + qoff[m]);
+            }
+            const float4 t = sv[w][8 * p + es];
+            const u64 tt[4] = {f2_dup(t.x), f2_dup(t.y), f2_dup(t.z), f2_dup(t.w)};
+#pragma unroll
+            for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+              for (int m = 0; m < NQ; ++m) {
+                acc[v][m][0] = f2_fma(tt[v], x[m].x, acc[v][m][0]);
+                acc[v][m][1] = f2_fma(tt[v], x[m].y, acc[v][m][1]);
+              }
+            if (p + 1 < steps) {
+#pragma unroll
+              for (int m = 0; m < NQ; ++m) x[m] = xn[m];
             }
           }
         }
       }
+      // sum the 8 entry slots (lanes cq, cq + 4, ..., cq + 28)
+#pragma unroll
+      for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+        for (int m = 0; m < NQ; ++m)
+#pragma unroll
+          for (int o = 4; o < 32; o <<= 1) {
+            acc[v][m][0] = f2_add(acc[v][m][0], f2_shfl_xor(acc[v][m][0], o));
+            acc[v][m][1] = f2_add(acc[v][m][1], f2_shfl_xor(acc[v][m][1], o));
+          }
+      if (wh == 1 && es == 0) {
+#pragma unroll
+        for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) red[gl][cq][v][m] = make_ulonglong2(acc[v][m][0], acc[v][m][1]);
+      }
+      pair_sync(1 + gl);
+      if (wh == 0 && es == 0) {
+#pragma unroll
+        for (int v = 0; v < kGroup; ++v) {
+          const int vv = g * kGroup + v;
+          if (vv < V) {
+#pragma unroll
+            for (int m = 0; m < NQ; ++m) {
+              if (EXACT || qb + m < nq) {
+                const ulonglong2 o = red[gl][cq][v][m];
+                const u64 s0 = f2_add(acc[v][m][0], o.x), s1 = f2_add(acc[v][m][1], o.y);
+                reinterpret_cast<ulonglong2*>(R + (long long)vv * ncols)[qb + m] = make_ulonglong2(s0, s1);
+              }
+            }
+          }
+        }
+      }
+      pair_sync(1 + gl);
     }
-    __syncthreads();
   }
 }
 
@@ -452,14 +523,17 @@ haar_status_t launch_shade_csr_f32(const float* vals, const uint16_t* idx, const
 }
 
 haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, const int32_t* gptr, int V,
-                                    const float* L, int NL, int ncols, float* R, cudaStream_t st) {
+                                    const float* L, int NL, int ncols, float* R, int* status, cudaStream_t st) {
+  (void)status;
+  const int nq = ncols / 4;
   const long long groups = (V + kGroup - 1) / kGroup;
   const unsigned nb = (unsigned)((groups + 3) / 4);
-  const int nq = ncols / 4;
-  if (nq <= 4) k_shade_gcsr_f32<1><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else if (nq <= 8) k_shade_gcsr_f32<2><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else if (nq <= 12) k_shade_gcsr_f32<3><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else k_shade_gcsr_f32<4><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  if (nq == 12) k_shade_gcsr_f32<3, true><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq == 8) k_shade_gcsr_f32<2, true><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq == 4) k_shade_gcsr_f32<1, true><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq <= 4) k_shade_gcsr_f32<1, false><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq <= 8) k_shade_gcsr_f32<2, false><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
+  else k_shade_gcsr_f32<3, false><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);   // 48-column passes
   return cuda_check(cudaGetLastError(), "k_shade_gcsr_f32 launch");
 }
 

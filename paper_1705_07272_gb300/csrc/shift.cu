@@ -179,10 +179,11 @@ __device__ __forceinline__ float block4(const ShiftArgs& a, const ShiftParam* p,
 // (gr0, gc0) = level-lvl0 grid position of the image's element (0, 0).
 template <int OUT>
 __device__ void haar_pass(const ShiftArgs& a, const ShiftParam* p, int s, int c, const float* src,
-                          float* dst, int rows, int cols, int lvl0, int sb, int gr0, int gc0) {
+                          float* dst, int rows, int cols, int lvl0, int sb, int gr0, int gc0,
+                          int tid, int nthr) {
   const int nbr = rows / sb, nbc = cols / sb;
   const int sh = __ffs(nbc) - 1;              // nbc is a power of two
-  for (int b = threadIdx.x; b < nbr * nbc; b += blockDim.x) {
+  for (int b = tid; b < nbr * nbc; b += nthr) {
     const int by = b >> sh, bx = b & (nbc - 1);
     if (sb == 4) {
       float x[16];
@@ -215,7 +216,8 @@ __device__ float tile_levels(const ShiftArgs& a, const ShiftParam* p, int s, int
   while (lvl < a.g.Lt) {
     const int sb = (a.g.Lt - lvl >= 2) ? 4 : 2;
     __syncthreads();
-    haar_pass<OUT>(a, p, s, c, src, dst, side, side, lvl, sb, (tr * T) >> lvl, (tc * T) >> lvl);
+    haar_pass<OUT>(a, p, s, c, src, dst, side, side, lvl, sb, (tr * T) >> lvl, (tc * T) >> lvl, threadIdx.x,
+                   blockDim.x);
     side /= sb;
     lvl += (sb == 4) ? 2 : 1;
     float* t = src; src = dst; dst = t;
@@ -225,30 +227,43 @@ __device__ float tile_levels(const ShiftArgs& a, const ShiftParam* p, int s, int
 }
 
 // Coarse levels Lt+1..n from the (H/T) x (W/T) image of tile means in img
-// (scratch: img2, same size / 16), then the scaling coefficients A_n.
-template <int OUT>
-__device__ void coarse_levels(const ShiftArgs& a, const ShiftParam* p, int s, int c, float* img,
-                              float* img2) {
+// (scratch: img2, same size / 16), then the scaling coefficients A_n.  WARP:
+// run by one warp (tid = lane) instead of the whole block.
+template <int OUT, bool WARP>
+__device__ void coarse_levels_t(const ShiftArgs& a, const ShiftParam* p, int s, int c, float* img,
+                                float* img2, int tid, int nthr) {
   const Geometry& g = a.g;
   int rows = g.tiles_r, cols = g.tiles_c, lvl = g.Lt;
   float* src = img;
   float* dst = img2;
   while (lvl < g.n) {
     const int sb = (g.n - lvl >= 2) ? 4 : 2;
-    __syncthreads();
-    haar_pass<OUT>(a, p, s, c, src, dst, rows, cols, lvl, sb, 0, 0);
+    if (WARP) __syncwarp(); else __syncthreads();
+    haar_pass<OUT>(a, p, s, c, src, dst, rows, cols, lvl, sb, 0, 0, tid, nthr);
     rows /= sb;
     cols /= sb;
     lvl += (sb == 4) ? 2 : 1;
     float* t = src; src = dst; dst = t;
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < g.q; k += blockDim.x) {
+  if (WARP) __syncwarp(); else __syncthreads();
+  for (int k = tid; k < g.q; k += nthr) {
     float v = src[k];
     if (p != nullptr && ((p->perm_mask >> (g.n + 1)) & 1u)) v = perm_value(a, *p, c, g.n + 1, 0, 0, k);
     put<OUT>(a, s, c, k, v);
   }
-  __syncthreads();
+  if (WARP) __syncwarp(); else __syncthreads();
+}
+
+template <int OUT>
+__device__ __forceinline__ void coarse_levels(const ShiftArgs& a, const ShiftParam* p, int s, int c, float* img,
+                                              float* img2) {
+  coarse_levels_t<OUT, false>(a, p, s, c, img, img2, threadIdx.x, blockDim.x);
+}
+
+template <int OUT>
+__device__ __forceinline__ void coarse_levels_warp(const ShiftArgs& a, const ShiftParam* p, int s, int c,
+                                                   float* img, float* img2, int lane) {
+  coarse_levels_t<OUT, true>(a, p, s, c, img, img2, lane, 32);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -368,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   if (!s_last) return;
   __threadfence();
   float* img = pbuf;
-  float* img2 = pbuf + g.n_tiles;
+  float* img2 = pbuf + ((g.n_tiles + 3) & ~3);   // float4-aligned
   for (int c = 0; c < g.C; ++c) {
     for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
       img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
@@ -392,13 +407,13 @@ __device__ __forceinline__ int morton_y(int t) { return morton_x(t >> 1); }
 // must call it.
 template <int OUT>
 __device__ __forceinline__ float merge4(const ShiftArgs& a, const ShiftParam* p, int s, int c, float A, int lane,
-                                        int st, int lvl, int i0, int j0, int by, int bx, int limit = 32) {
+                                        int st, int sh, int lvl, int i0, int j0, int by, int bx, int limit = 32) {
   const int base = lane & ~(4 * st - 1);
   const float e0 = __shfl_sync(0xffffffffu, A, base);
   const float e1 = __shfl_sync(0xffffffffu, A, base + st);
   const float e2 = __shfl_sync(0xffffffffu, A, base + 2 * st);
   const float e3 = __shfl_sync(0xffffffffu, A, base + 3 * st);
-  const int m = (lane - base) / st;
+  const int m = (lane - base) >> sh;
   if ((lane & (st - 1)) == 0 && m < 3 && lane < limit) {
     const float d = (m == 0) ? 0.5f * ((e1 + e3) - (e0 + e2))
                   : (m == 1) ? 0.5f * ((e2 + e3) - (e0 + e1)) : 0.5f * ((e0 + e3) - (e1 + e2));
@@ -415,22 +430,95 @@ __device__ __forceinline__ float merge4(const ShiftArgs& a, const ShiftParam* p,
   return 0.5f * ((e0 + e1) + (e2 + e3));
 }
 
+__device__ __forceinline__ float f4c(const float4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Bilinear resample of a translated 4 x 4 block from the source window held
+// as 5 rows x 8 aligned columns: row r, column q of the block reads window
+// columns O + q and O + q + 1 (O = the shift's column phase, uniform per
+// launch); wx1 weights column q, wx0 column q + 1 (likewise along rows).
+template <int O>
+__device__ __forceinline__ void bilin_tr(const float4 (&v)[5][2], float wx0, float wx1, float wy0, float wy1,
+                                         float (&x)[16]) {
+  float h[5][4];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c0 = O + q, c1 = O + q + 1;
+      const float w0 = f4c(v[r][c0 >> 2], c0 & 3), w1 = f4c(v[r][c1 >> 2], c1 & 3);
+      h[r][q] = wx0 * w1 + wx1 * w0;
+    }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[4 * r + q] = wy0 * h[r + 1][q] + wy1 * h[r][q];
+}
+
+// Levels 1-2 of the thread's 4 x 4 block: writes the 15 detail coefficients
+// and returns the level-2 scaling value.  fast: float32 output, k
+// contiguous, no permuted level, levels 1-2 untruncated, and x pre-scaled by
+// 1/2 (exact), so that level 1 needs no multiplies; the level-1
+// coefficients then leave as three 2 x 2 patches of float2 stores.
+template <int OUT>
+__device__ __forceinline__ float levels12(const ShiftArgs& a, const ShiftParam* p, int s, int c, const float (&x)[16],
+                                          bool fast, int tr, int tc, int by, int bx) {
+  const Geometry& g = a.g;
+  const int T = g.T;
+  if (!fast) return block4<OUT>(a, p, s, c, x, 0, tr * T, tc * T, by, bx);
+  const int g1 = g.q << (2 * (g.n - 1)), g2 = g.q << (2 * (g.n - 2));
+  float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)c * a.st_c;
+  float A1[4], D1[3][4];
+#pragma unroll
+  for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+    for (int sc = 0; sc < 2; ++sc) {
+      const float ea = x[(2 * sa) * 4 + 2 * sc], eb = x[(2 * sa) * 4 + 2 * sc + 1];
+      const float ec = x[(2 * sa + 1) * 4 + 2 * sc], ed = x[(2 * sa + 1) * 4 + 2 * sc + 1];
+      A1[2 * sa + sc] = (ea + eb) + (ec + ed);
+      D1[0][2 * sa + sc] = (eb + ed) - (ea + ec);
+      D1[1][2 * sa + sc] = (ec + ed) - (ea + eb);
+      D1[2][2 * sa + sc] = (ea + ed) - (eb + ec);
+    }
+  const int cols1 = g.W >> 1, cols2 = g.W >> 2;
+  const int r1 = ((tr * T) >> 1) + 2 * by, c1 = ((tc * T) >> 1) + 2 * bx;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    float* pb = ob + g1 * (1 + b) + r1 * cols1 + c1;
+    *reinterpret_cast<float2*>(pb) = make_float2(D1[b][0], D1[b][1]);
+    *reinterpret_cast<float2*>(pb + cols1) = make_float2(D1[b][2], D1[b][3]);
+  }
+  const float ea = A1[0], eb = A1[1], ec = A1[2], ed = A1[3];
+  if (4 * g2 <= a.K) {
+    float* p2 = ob + (((tr * T) >> 2) + by) * cols2 + ((tc * T) >> 2) + bx;
+    p2[g2] = 0.5f * ((eb + ed) - (ea + ec));
+    p2[2 * g2] = 0.5f * ((ec + ed) - (ea + eb));
+    p2[3 * g2] = 0.5f * ((ea + ed) - (eb + ec));
+  }
+  return 0.5f * ((ea + eb) + (ec + ed));
+}
+
+__device__ __forceinline__ void named_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
 // Register path for 32 x 32 and 64 x 64 tiles: every thread resamples its own
-// 4 x 4 block of output pixels straight from the L2-resident pixel map
-// (translation: the 5 x 5 source window, all 25 loads in flight; rotation:
-// 4 bilinear taps per pixel and channel), runs levels 1-2 in registers,
-// writes them, and leaves the block's scaling value in shared memory for the
-// remaining tile levels.  blockDim = (T/4)^2.
-template <int KIND, int OUT>
-__global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
+// 4 x 4 block of output pixels for up to CG channels straight from
+// the L2-resident pixel map (translation: a 5 x 8 aligned window of float4
+// loads per channel; rotation: 4 bilinear taps per pixel and channel at
+// shared coordinates), runs levels 1-2 in registers and writes them; levels
+// 3-4 merge Morton-consecutive lanes by shuffles.  The other warps then
+// leave, and warp 0 finishes the tile's levels 5-6 from shared memory, hands
+// the tile mean on, and (last tile of a shift) runs the coarse levels.
+// blockDim = (T/4)^2.
+template <int KIND, int OUT, int CG>
+__global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift_reg(ShiftArgs a) {
   extern __shared__ __align__(16) float smem[];
-  __shared__ int s_last;
   const Geometry& g = a.g;
   const int T = g.T;
   const int nb = T >> 2;
   const int tile = blockIdx.x, s = blockIdx.y, cgrp = blockIdx.z;
   const int tr = tile / g.tiles_c, tc = tile - tr * g.tiles_c;
-  constexpr int CG = (KIND == KIND_ROTATE) ? kRotChannels : 1;
   const int c0 = cgrp * CG;
   const int cgn = min(CG, g.C - c0);
   __shared__ ShiftParam s_prm;
@@ -442,13 +530,18 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
   const int by = morton_y(threadIdx.x), bx = morton_x(threadIdx.x);
   const int i0 = tr * T + 4 * by, j0 = tc * T + 4 * bx;
   const int Wm = g.W - 1;
-  float* sA = smem;                                 // [CG][nb * nb]
+  const int g1 = g.q << (2 * (g.n - 1));
+  const bool fast = OUT == HAAR_OUT_F32 && a.st_k == 1 && a.scale == 1.0f && (p == nullptr || p->perm_mask == 0u) &&
+                    4 * g1 <= a.K && g.n >= 2;
+  const float hsc = fast ? 0.5f : 1.0f;
 
-  float x[CG][16];
+  float a2[CG];
   if (KIND == KIND_TRANSLATE) {
     const ShiftParam pr = *p;
-    const float* F = a.pix + (long long)c0 * g.N;
-    int ro[5], cs[5];
+    // source rows (pole crossings mirror the row and move half a turn) and
+    // the 16-byte aligned first column of each row's window
+    const int o = (-(pr.kx + 1)) & 3;                 // column phase, the same for every row
+    int ro[5], ca[5];
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
       int i = i0 - pr.ky - 1 + r, sh = 0;
@@ -462,26 +555,37 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
         }
       }
       ro[r] = i * g.W;
-      cs[r] = j0 - pr.kx - 1 + (sh ? (g.W >> 1) : 0);
+      ca[r] = j0 - pr.kx - 1 + (sh ? (g.W >> 1) : 0) - o;
     }
-    float w[5][5];
+    const float wx0 = pr.wx0, wx1 = pr.wx1, wy0 = pr.wy0 * hsc, wy1 = pr.wy1 * hsc;
 #pragma unroll
-    for (int r = 0; r < 5; ++r)
+    for (int ci = 0; ci < CG; ++ci) {
+      if (ci < cgn) {
+        const float* F = a.pix + (long long)(c0 + ci) * g.N;
+        float4 v[5][2];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) w[r][q] = __ldg(F + ro[r] + ((cs[r] + q) & Wm));
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        x[0][4 * r + q] = pr.wy0 * (pr.wx0 * w[r + 1][q + 1] + pr.wx1 * w[r + 1][q]) +
-                          pr.wy1 * (pr.wx0 * w[r][q + 1] + pr.wx1 * w[r][q]);
+        for (int r = 0; r < 5; ++r) {
+          v[r][0] = __ldg(reinterpret_cast<const float4*>(F + ro[r] + (ca[r] & Wm)));
+          v[r][1] = __ldg(reinterpret_cast<const float4*>(F + ro[r] + ((ca[r] + 4) & Wm)));
+        }
+        float x[16];
+        switch (o) {
+          case 0: bilin_tr<0>(v, wx0, wx1, wy0, wy1, x); break;
+          case 1: bilin_tr<1>(v, wx0, wx1, wy0, wy1, x); break;
+          case 2: bilin_tr<2>(v, wx0, wx1, wy0, wy1, x); break;
+          default: bilin_tr<3>(v, wx0, wx1, wy0, wy1, x); break;
+        }
+        a2[ci] = levels12<OUT>(a, p, s, c0 + ci, x, fast, tr, tc, by, bx);
+      }
+    }
   } else if (KIND == KIND_ROTATE) {
     const ShiftParam pr = *p;
+    float x[CG][16];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int i = i0 + r;
       const float st = __ldg(a.trig + i), ct = __ldg(a.trig + g.H + i);
-      long long off[4][4];
+      int off[4][4];
       float fu[4], fv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -509,10 +613,10 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
           if (r1 < 0) { r1 = -1 - r1; h1 = g.W >> 1; }
           if (r1 >= g.H) { r1 = 2 * g.H - 1 - r1; h1 = g.W >> 1; }
         }
-        off[q][0] = (long long)r0 * g.W + ((ja + h0) & Wm);
-        off[q][1] = (long long)r0 * g.W + ((ja + 1 + h0) & Wm);
-        off[q][2] = (long long)r1 * g.W + ((ja + h1) & Wm);
-        off[q][3] = (long long)r1 * g.W + ((ja + 1 + h1) & Wm);
+        off[q][0] = r0 * g.W + ((ja + h0) & Wm);
+        off[q][1] = r0 * g.W + ((ja + 1 + h0) & Wm);
+        off[q][2] = r1 * g.W + ((ja + h1) & Wm);
+        off[q][3] = r1 * g.W + ((ja + 1 + h1) & Wm);
       }
 #pragma unroll
       for (int ci = 0; ci < CG; ++ci) {
@@ -524,126 +628,245 @@ __global__ void __launch_bounds__(kThreads) k_shift_reg(ShiftArgs a) {
 #pragma unroll
             for (int t = 0; t < 4; ++t) f[q][t] = __ldg(F + off[q][t]);
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            x[ci][4 * r + q] = (1.0f - fu[q]) * ((1.0f - fv[q]) * f[q][0] + fv[q] * f[q][1]) +
-                               fu[q] * ((1.0f - fv[q]) * f[q][2] + fv[q] * f[q][3]);
+          for (int q = 0; q < 4; ++q) {
+            const float w0 = (1.0f - fu[q]) * hsc, w1 = fu[q] * hsc;
+            x[ci][4 * r + q] = w0 * ((1.0f - fv[q]) * f[q][0] + fv[q] * f[q][1]) +
+                               w1 * ((1.0f - fv[q]) * f[q][2] + fv[q] * f[q][3]);
+          }
         }
       }
     }
+#pragma unroll
+    for (int ci = 0; ci < CG; ++ci)
+      if (ci < cgn) a2[ci] = levels12<OUT>(a, p, s, c0 + ci, x[ci], fast, tr, tc, by, bx);
   } else {  // KIND_COPY
     const float* F = a.pix + (long long)s * g.N;
+    float x[16];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const float4 t = __ldg(reinterpret_cast<const float4*>(F + (long long)(i0 + r) * g.W + j0));
-      x[0][4 * r] = t.x; x[0][4 * r + 1] = t.y; x[0][4 * r + 2] = t.z; x[0][4 * r + 3] = t.w;
+      x[4 * r] = t.x * hsc; x[4 * r + 1] = t.y * hsc; x[4 * r + 2] = t.z * hsc; x[4 * r + 3] = t.w * hsc;
     }
-  }
-  // Fast store path (float32, coefficients contiguous in k, no permuted
-  // level, levels 1-2 kept whole): the thread's level-1 coefficients are
-  // three 2 x 2 patches (one per band) written as float2 pairs.
-  const int g1 = g.q << (2 * (g.n - 1)), g2 = g.q << (2 * (g.n - 2));
-  const bool fast = OUT == HAAR_OUT_F32 && a.st_k == 1 && a.scale == 1.0f && (p == nullptr || p->perm_mask == 0u) &&
-                    4 * g1 <= a.K && g.n >= 2;
-  float a2[CG];
-#pragma unroll
-  for (int ci = 0; ci < CG; ++ci) {
-    if (ci >= cgn) continue;
-    if (fast) {
-      float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)(c0 + ci) * a.st_c;
-      const float* xb = x[ci];
-      float A1[4], D1[3][4];
-#pragma unroll
-      for (int sa = 0; sa < 2; ++sa)
-#pragma unroll
-        for (int sc = 0; sc < 2; ++sc) {
-          const float ea = xb[(2 * sa) * 4 + 2 * sc], eb = xb[(2 * sa) * 4 + 2 * sc + 1];
-          const float ec = xb[(2 * sa + 1) * 4 + 2 * sc], ed = xb[(2 * sa + 1) * 4 + 2 * sc + 1];
-          A1[2 * sa + sc] = 0.5f * ((ea + eb) + (ec + ed));
-          D1[0][2 * sa + sc] = 0.5f * ((eb + ed) - (ea + ec));
-          D1[1][2 * sa + sc] = 0.5f * ((ec + ed) - (ea + eb));
-          D1[2][2 * sa + sc] = 0.5f * ((ea + ed) - (eb + ec));
-        }
-      const int cols1 = g.W >> 1, cols2 = g.W >> 2;
-      const int r1 = ((tr * T) >> 1) + 2 * by, c1 = ((tc * T) >> 1) + 2 * bx;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        float* pb = ob + (long long)g1 * (1 + b) + (long long)r1 * cols1 + c1;
-        *reinterpret_cast<float2*>(pb) = make_float2(D1[b][0], D1[b][1]);
-        *reinterpret_cast<float2*>(pb + cols1) = make_float2(D1[b][2], D1[b][3]);
-      }
-      const float ea = A1[0], eb = A1[1], ec = A1[2], ed = A1[3];
-      if (4 * g2 <= a.K) {
-        float* p2 = ob + ((long long)((tr * T) >> 2) + by) * cols2 + ((tc * T) >> 2) + bx;
-        p2[g2] = 0.5f * ((eb + ed) - (ea + ec));
-        p2[2 * g2] = 0.5f * ((ec + ed) - (ea + eb));
-        p2[3 * g2] = 0.5f * ((ea + ed) - (eb + ec));
-      }
-      a2[ci] = 0.5f * ((ea + eb) + (ec + ed));
-    } else {
-      a2[ci] = block4<OUT>(a, p, s, c0 + ci, x[ci], 0, tr * T, tc * T, by, bx);
-    }
+    a2[0] = levels12<OUT>(a, p, s, 0, x, fast, tr, tc, by, bx);
   }
 
-  // levels 3..Lt: merges of 4 Morton-consecutive values, first inside each
-  // warp (shuffles, lanes in groups of 4 then 16), then one warp finishes the
-  // tile from the per-group values left in shared memory
+  // levels 3 and 4: merges of 4 Morton-consecutive lanes (strides 1 and 4);
+  // one value per 16 lanes remains and goes to shared memory
   const int lane = threadIdx.x & 31;
   const int nthreads = nb * nb;
+  const int groups = nthreads >> 4;
+  float* sA = smem;                                 // [CG][groups]
+#pragma unroll
+  for (int ci = 0; ci < CG; ++ci) {
+    if (ci < cgn) {
+      float A = merge4<OUT>(a, p, s, c0 + ci, a2[ci], lane, 1, 0, 3, tr * T, tc * T, by, bx);
+      A = merge4<OUT>(a, p, s, c0 + ci, A, lane, 4, 2, 4, tr * T, tc * T, by, bx);
+      if ((lane & 15) == 0) sA[ci * groups + (threadIdx.x >> 4)] = A;
+    }
+  }
+  if (threadIdx.x >= 32) {
+    named_arrive(1, nthreads);
+    return;
+  }
+  named_sync(1, nthreads);
+
+  // warp 0: levels 5..Lt on the `groups` values of each channel (a Morton-
+  // ordered grid of 16 x 16-pixel blocks)
+  const int gy = morton_y(lane) << 2, gx = morton_x(lane) << 2;
   for (int ci = 0; ci < cgn; ++ci) {
     const int c = c0 + ci;
-    float A = a2[ci];
-    int lvl = 2;
-    int st = 1;                                     // lane stride between the 4 merged values
+    float B = (lane < groups) ? sA[ci * groups + lane] : 0.0f;
+    int st2 = 1, sh2 = 0;
+    for (int lvl = 4; lvl < g.Lt; ++lvl) {
+      B = merge4<OUT>(a, p, s, c, B, lane, st2, sh2, lvl + 1, tr * T, tc * T, gy, gx, groups);
+      st2 *= 4;
+      sh2 += 2;
+    }
+    if (lane == 0) {
+      if (a.means != nullptr)
+        a.means[((long long)s * g.C + c) * g.n_tiles + tile] = B;
+      else
+        reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = B;
+    }
+  }
+  if (a.counters == nullptr) return;
+  unsigned last = 0;
+  if (lane == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(a.counters + s, 1u);
+    last = (t == (unsigned)(g.n_tiles * gridDim.z - 1)) ? 1u : 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  float* img = smem;
+  float* img2 = smem + ((g.n_tiles + 3) & ~3);   // float4-aligned
+  for (int c = 0; c < g.C; ++c) {
+    for (int t = lane; t < g.n_tiles; t += 32)
+      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
+    coarse_levels_warp<OUT>(a, p, s, c, img, img2, lane);
+  }
+  if (lane == 0) a.counters[s] = 0u;
+}
+
+// Coefficient-major translation kernel: one CTA takes a 16 x 16 output tile
+// for a group of up to kKscPlanes (shift, channel) planes, one thread per
+// (plane, 4 x 4 block).  Levels 1-4 of every plane are staged in shared
+// memory as [coefficient][plane] and leave as whole rows of the KSC output
+// (the group's consecutive floats of each coefficient), so the stores are
+// coalesced instead of one float per 32-byte sector.  The tile means go to
+// the workspace; the last tile of a plane group runs the coarse levels of
+// all its planes at once (16 threads per plane).
+constexpr int kKscPlanes = 48;
+constexpr int kKscPitch = kKscPlanes + 1;       // staging row pitch (bank spread)
+
+// shared floats per plane in the coarse pass: the tile-mean image and the
+// scratch image of the next two levels, each rounded to whole float4
+__host__ __device__ __forceinline__ int ksc_plane_floats(long long n_tiles) {
+  return (int)(((n_tiles + 3) & ~3LL) + ((n_tiles / 16 + 4) & ~3LL));
+}
+
+__device__ __forceinline__ int ksc_global_k(const Geometry& g, int kl, int tr, int tc) {
+  int lvl, b, r, col;
+  if (kl < 192) { lvl = 1; b = kl >> 6; r = (kl >> 3) & 7; col = kl & 7; }
+  else if (kl < 240) { lvl = 2; const int k2 = kl - 192; b = k2 >> 4; r = (k2 >> 2) & 3; col = k2 & 3; }
+  else if (kl < 252) { lvl = 3; const int k3 = kl - 240; b = k3 >> 2; r = (k3 >> 1) & 1; col = k3 & 1; }
+  else { lvl = 4; b = kl - 252; r = 0; col = 0; }
+  const int side = 16 >> lvl;
+  const int gl = g.q << (2 * (g.n - lvl));
+  return gl * (1 + b) + (tr * side + r) * (g.W >> lvl) + tc * side + col;
+}
+
+__global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int P) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_last;
+  const Geometry& g = a.g;                      // T = 16, Lt = 4
+  const int tile = blockIdx.x;
+  const int tr = tile / g.tiles_c, tc = tile - tr * g.tiles_c;
+  const int p0 = blockIdx.y * kKscPlanes;
+  const int PG = min(kKscPlanes, P - p0);
+  const int t = threadIdx.x;
+  const int pl = t >> 4, blk = t & 15, lane = t & 31;
+  const bool on = pl < PG;
+  const int plane = p0 + (on ? pl : PG - 1);
+  const int s = plane / g.C, c = plane - s * g.C;
+  const ShiftParam* pp = a.prm + s;
+  const ShiftParam pr = *pp;
+  const int by = morton_y(blk), bx = morton_x(blk);
+  const int i0 = tr * 16 + 4 * by, j0 = tc * 16 + 4 * bx;
+  const int Wm = g.W - 1;
+  float* stage = smem;                          // [255][kKscPitch]
+
+  // resample (translation: 5 x 8 aligned window, pre-scaled by 1/2) and levels 1-2
+  const int o = (-(pr.kx + 1)) & 3;
+  const float* F = a.pix + (long long)c * g.N;
+  float4 v[5][2];
 #pragma unroll
-    for (int step = 0; step < 2; ++step) {
-      if (lvl >= g.Lt || 4 * st > nthreads || 4 * st > 32) break;
-      A = merge4<OUT>(a, p, s, c, A, lane, st, lvl + 1, tr * T, tc * T, by, bx);
-      ++lvl;
-      st *= 4;
-    }
-    // one value per group of st threads remains
-    const int groups = nthreads / st;
-    __syncthreads();
-    if ((threadIdx.x & (st - 1)) == 0) sA[threadIdx.x / st] = A;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      // the remaining levels on `groups` values (a Morton-ordered grid of blocks of side 2^lvl)
-      float B = (lane < groups) ? sA[lane] : 0.0f;
-      const int l1 = lvl;                         // group lane = Morton index of a level-l1 block
-      const int gy = morton_y(lane) << (l1 - 2), gx = morton_x(lane) << (l1 - 2);
-      int st2 = 1;
-      while (lvl < g.Lt) {
-        B = merge4<OUT>(a, p, s, c, B, lane, st2, lvl + 1, tr * T, tc * T, gy, gx, groups);
-        ++lvl;
-        st2 *= 4;
-      }
-      if (lane == 0) {
-        if (a.means != nullptr)
-          a.means[((long long)s * g.C + c) * g.n_tiles + tile] = B;
-        else
-          reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = B;
+  for (int r = 0; r < 5; ++r) {
+    int i = i0 - pr.ky - 1 + r, sh = 0;
+    if (g.boundary == HAAR_BOUNDARY_TORUS) {
+      i &= (g.H - 1);
+    } else {
+#pragma unroll 1
+      for (int it = 0; it < 8 && (i < 0 || i >= g.H); ++it) {
+        i = (i < 0) ? -1 - i : 2 * g.H - 1 - i;
+        sh ^= 1;
       }
     }
+    const int ca = j0 - pr.kx - 1 + (sh ? (g.W >> 1) : 0) - o;
+    v[r][0] = __ldg(reinterpret_cast<const float4*>(F + i * g.W + (ca & Wm)));
+    v[r][1] = __ldg(reinterpret_cast<const float4*>(F + i * g.W + ((ca + 4) & Wm)));
+  }
+  float x[16];
+  const float wy0 = 0.5f * pr.wy0, wy1 = 0.5f * pr.wy1;
+  switch (o) {
+    case 0: bilin_tr<0>(v, pr.wx0, pr.wx1, wy0, wy1, x); break;
+    case 1: bilin_tr<1>(v, pr.wx0, pr.wx1, wy0, wy1, x); break;
+    case 2: bilin_tr<2>(v, pr.wx0, pr.wx1, wy0, wy1, x); break;
+    default: bilin_tr<3>(v, pr.wx0, pr.wx1, wy0, wy1, x); break;
+  }
+  const unsigned pm = pr.perm_mask;
+  float A1[4];
+#pragma unroll
+  for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+    for (int sc = 0; sc < 2; ++sc) {
+      const float ea = x[(2 * sa) * 4 + 2 * sc], eb = x[(2 * sa) * 4 + 2 * sc + 1];
+      const float ec = x[(2 * sa + 1) * 4 + 2 * sc], ed = x[(2 * sa + 1) * 4 + 2 * sc + 1];
+      A1[2 * sa + sc] = (ea + eb) + (ec + ed);
+      const float d[3] = {(eb + ed) - (ea + ec), (ec + ed) - (ea + eb), (ea + ed) - (eb + ec)};
+      const int r = 2 * by + sa, col = 2 * bx + sc;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        float val = d[b];
+        if (pm & 2u) val = perm_value(a, pr, c, 1, b, tr * 8 + r, tc * 8 + col);
+        if (on) stage[(b * 64 + r * 8 + col) * kKscPitch + pl] = val;
+      }
+    }
+  float A;
+  {
+    const float ea = A1[0], eb = A1[1], ec = A1[2], ed = A1[3];
+    const float d[3] = {0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)), 0.5f * ((ea + ed) - (eb + ec))};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float val = d[b];
+      if (pm & 4u) val = perm_value(a, pr, c, 2, b, tr * 4 + by, tc * 4 + bx);
+      if (on) stage[(192 + b * 16 + by * 4 + bx) * kKscPitch + pl] = val;
+    }
+    A = 0.5f * ((ea + eb) + (ec + ed));
+  }
+  // levels 3 and 4 within the plane's 16 lanes (Morton order: strides 1, 4)
+#pragma unroll
+  for (int step = 0; step < 2; ++step) {
+    const int st = step ? 4 : 1, lvl = 3 + step;
+    const int base = lane & ~(4 * st - 1);
+    const float e0 = __shfl_sync(0xffffffffu, A, base);
+    const float e1 = __shfl_sync(0xffffffffu, A, base + st);
+    const float e2 = __shfl_sync(0xffffffffu, A, base + 2 * st);
+    const float e3 = __shfl_sync(0xffffffffu, A, base + 3 * st);
+    const int m = (lane - base) >> (2 * step);
+    if ((lane & (st - 1)) == 0 && m < 3) {
+      float val = (m == 0) ? 0.5f * ((e1 + e3) - (e0 + e2))
+                : (m == 1) ? 0.5f * ((e2 + e3) - (e0 + e1)) : 0.5f * ((e0 + e3) - (e1 + e2));
+      const int rr = by >> (lvl - 2), cc = bx >> (lvl - 2);
+      if ((pm >> lvl) & 1u) val = perm_value(a, pr, c, lvl, m, tr * (16 >> lvl) + rr, tc * (16 >> lvl) + cc);
+      const int kl = (lvl == 3) ? 240 + m * 4 + rr * 2 + cc : 252 + m;
+      if (on) stage[kl * kKscPitch + pl] = val;
+    }
+    A = 0.5f * ((e0 + e1) + (e2 + e3));
+  }
+  if (blk == 0 && on) {
+    a.means[(long long)plane * g.n_tiles + tile] = A;
+    __threadfence();
   }
   __syncthreads();
 
-  if (a.counters == nullptr) return;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(a.counters + s, 1u);
-    s_last = (t == (unsigned)(g.n_tiles * gridDim.z - 1)) ? 1 : 0;
+  // rows of the group's PG consecutive floats, coefficient by coefficient
+  float* out = reinterpret_cast<float*>(a.out);
+  for (int e = t; e < 255 * PG; e += blockDim.x) {
+    const int kl = e / PG, q = e - kl * PG;
+    const int k = ksc_global_k(g, kl, tr, tc);
+    if (k < a.K) out[(long long)k * P + p0 + q] = stage[kl * kKscPitch + q];
+  }
+
+  if (t == 0) {
+    const unsigned n = atomicAdd(a.counters + blockIdx.y, 1u);
+    s_last = (n == (unsigned)(g.n_tiles - 1)) ? 1 : 0;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  float* img = smem;
-  float* img2 = smem + g.n_tiles;
-  for (int c = 0; c < g.C; ++c) {
-    for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
-      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
-    coarse_levels<OUT>(a, p, s, c, img, img2);
-  }
-  if (threadIdx.x == 0) a.counters[s] = 0u;
+  // coarse levels of every plane of the group, 16 threads per plane; both
+  // images start on 16-byte boundaries (the passes read them as float4)
+  const int nt4 = (g.n_tiles + 3) & ~3;
+  const int per = ksc_plane_floats(g.n_tiles);
+  float* img = smem + pl * per;
+  float* img2 = img + nt4;
+  if (on)
+    for (int k = blk; k < g.n_tiles; k += 16) img[k] = __ldcg(a.means + (long long)plane * g.n_tiles + k);
+  // threads of absent planes (partial group) take part in the barriers only
+  coarse_levels_t<HAAR_OUT_F32, false>(a, pp, s, c, img, img2, on ? blk : (1 << 30), 16);
+  if (t == 0) a.counters[blockIdx.y] = 0u;
 }
 
 // Coarse levels of the forward transform, in place: one CTA per map.
@@ -652,7 +875,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_inplace(ShiftArgs a) {
   const int s = blockIdx.x;
   float* out = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s;
   float* img = smem;
-  float* img2 = smem + a.g.n_tiles;
+  float* img2 = smem + ((a.g.n_tiles + 3) & ~3);   // float4-aligned
   for (int t = threadIdx.x; t < a.g.n_tiles; t += blockDim.x) img[t] = out[t];
   __syncthreads();
   // put() multiplies by a.scale; the tile means were stored unscaled
@@ -796,24 +1019,40 @@ static size_t shift_smem_bytes(const Geometry& g, int kind) {
   return sizeof(float) * ((size_t)winr + pix + scratch);
 }
 
+template <int KIND, int OUT, int CG>
+static haar_status_t launch_reg(const ShiftArgs& a, int S, cudaStream_t st) {
+  const int nb = a.g.T / 4;
+  size_t fl = (size_t)CG * nb * nb + (size_t)(nb / 4) * (nb / 4) + 8;
+  const size_t coarse = (size_t)a.g.n_tiles + (size_t)a.g.n_tiles / 4 + 8;
+  if (fl < coarse) fl = coarse;
+  const size_t sm = fl * sizeof(float);
+  auto fr = k_shift_reg<KIND, OUT, CG>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_reg)");
+  }
+  dim3 grid(a.g.n_tiles, S, (a.g.C + CG - 1) / CG);
+  fr<<<grid, nb * nb, sm, st>>>(a);
+  return cuda_check(cudaGetLastError(), "k_shift_reg launch");
+}
+
+// Channels per thread: a rotation shares its coordinates across kRotChannels
+// channels; a translation shares only its window addresses, so it takes
+// kRotChannels channels per thread only when that still leaves several
+// waves of CTAs (otherwise one channel per CTA, for parallelism).
 template <int KIND, int OUT>
 static haar_status_t launch_k(const ShiftArgs& a, int S, cudaStream_t st) {
-  const int CG = (KIND == KIND_ROTATE) ? kRotChannels : 1;
   if (a.g.T >= 32) {
-    const int nb = a.g.T / 4;
-    size_t fl = (size_t)CG * nb * nb + (size_t)(nb / 4) * (nb / 4) + 8;
-    const size_t coarse = (size_t)a.g.n_tiles + (size_t)a.g.n_tiles / 4 + 8;
-    if (fl < coarse) fl = coarse;
-    const size_t sm = fl * sizeof(float);
-    auto fr = k_shift_reg<KIND, OUT>;
-    if (sm > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_reg)");
+    if constexpr (KIND == KIND_COPY) {
+      return launch_reg<KIND, OUT, 1>(a, S, st);
+    } else if constexpr (KIND == KIND_ROTATE) {
+      return launch_reg<KIND, OUT, kRotChannels>(a, S, st);
+    } else {
+      if ((long long)a.g.n_tiles * S >= 2432) return launch_reg<KIND, OUT, kRotChannels>(a, S, st);
+      return launch_reg<KIND, OUT, 1>(a, S, st);
     }
-    dim3 grid(a.g.n_tiles, S, (a.g.C + CG - 1) / CG);
-    fr<<<grid, nb * nb, sm, st>>>(a);
-    return cuda_check(cudaGetLastError(), "k_shift_reg launch");
   }
+  const int CG = (KIND == KIND_ROTATE) ? kRotChannels : 1;
   const size_t sm = shift_smem_bytes(a.g, KIND);
   auto fn = k_shift<KIND, OUT>;
   if (sm > 48 * 1024) {
@@ -859,8 +1098,58 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
   return cuda_check(cudaGetLastError(), "k_setup launch");
 }
 
+// The coefficient-major kernel serves F32 KSC translations whose tile-mean
+// workspace and shared-memory coarse pass fit.
+bool ksc_eligible(const haar_shift_desc_t& d, int S) {
+  if (d.kind != HAAR_SHIFT_TRANSLATE || d.out_type != HAAR_OUT_F32 || d.out_layout != HAAR_LAYOUT_KSC) return false;
+  if (d.height < 16) return false;
+  const long long P = (long long)S * d.channels;
+  if ((P + kKscPlanes - 1) / kKscPlanes > S) return false;                 // one counter per plane group
+  const long long n16 = (long long)(d.height / 16) * (d.width / 16);
+  return ksc_smem_floats(n16) * sizeof(float) <= 200 * 1024;
+}
+
+size_t ksc_means_floats(const haar_shift_desc_t& d, int S) {
+  return (size_t)S * d.channels * (size_t)(d.height / 16) * (d.width / 16);
+}
+
+size_t ksc_smem_floats(long long n16) {
+  const long long coarse = (long long)kKscPlanes * ksc_plane_floats(n16);
+  const long long stage = 255LL * kKscPitch;
+  return (size_t)(coarse > stage ? coarse : stage);
+}
+
+static haar_status_t launch_ksc(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out, cudaStream_t st) {
+  ShiftArgs a;
+  const Geometry g = make_geometry(p->geo.H, p->geo.W, p->geo.C, p->geo.boundary, 16);
+  a.g = g;
+  a.K = p->K;
+  const long long P = (long long)S * g.C;
+  a.st_s = g.C; a.st_c = 1; a.st_k = P;
+  a.plane = 0;
+  a.out = out;
+  a.pix = p->pix;
+  a.cin = coeffs_in;
+  a.prm = p->prm;
+  a.means = p->means;
+  a.counters = p->counters;
+  a.trig = p->trig;
+  a.scale = 1.0f;
+  a.u_scale = a.v_scale = 0.0f;
+  const size_t sm = ksc_smem_floats(g.n_tiles) * sizeof(float);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_shift_ksc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_ksc)");
+  }
+  dim3 grid(g.n_tiles, (unsigned)((P + kKscPlanes - 1) / kKscPlanes));
+  k_shift_ksc<<<grid, 16 * kKscPlanes, sm, st>>>(a, (int)P);
+  return cuda_check(cudaGetLastError(), "k_shift_ksc launch");
+}
+
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
                            cudaStream_t st) {
+  if (ksc_eligible(p->desc, S) && ksc_means_floats(p->desc, S) <= p->means_cap)
+    return launch_ksc(p, coeffs_in, S, out, st);
   ShiftArgs a;
   const Geometry& g = p->geo;
   a.g = g;

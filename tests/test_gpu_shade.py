@@ -115,7 +115,7 @@ def test_csr_ragged_rows(hs):
     assert rel_l2(got, ref) <= 1e-5
 
 
-def _group_reference(vals, idx, rowptr, V, G=4):
+def _group_reference(vals, idx, rowptr, V, G):
     """Union index list and [nnz][G] values of every group of G rows."""
     gptr, gidx, gvals = [0], [], []
     for g0 in range(0, V, G):
@@ -131,26 +131,54 @@ def _group_reference(vals, idx, rowptr, V, G=4):
     return np.array(gptr), np.concatenate(gidx), np.concatenate(gvals)
 
 
-def test_group_csr_packing_and_shading(hs):
+@pytest.mark.parametrize("S", [4, 16, 20])
+def test_group_csr_packing_and_shading(hs, S):
+    # S C = 12 (one partial column chunk), 48 (exact), 60 (two chunks); 777
+    # vertices leave a ragged last group
     import torch
-    sc = synth.scene(1, V=777, S=4, H=32, W=64)
+    sc = synth.scene(1, V=777, S=S, H=32, W=64)
     H, W = 32, 64
     vals, idx, rowptr = _csr_inputs(sc, 64, H, W)
     V = sc["V"]
+    # rows 16..31 (one whole group) and 40..43 empty, row 50 ragged, one index past
+    # the lighting (dropped by the packing)
+    lens = np.diff(rowptr)
+    lens[16:32] = 0
+    lens[40:44] = 0
+    lens[50] = 13
+    keep = np.concatenate([np.arange(rowptr[v], rowptr[v] + lens[v]) for v in range(V)])
+    vals, idx = vals[keep], idx[keep].copy()
+    rowptr = np.concatenate([[0], np.cumsum(lens)])
+    idx[rowptr[60] + 5] = H * W + 3
+    idx[rowptr[60]:rowptr[61]] = np.sort(idx[rowptr[60]:rowptr[61]])
     tr = hs.haar_transport_group(V, H * W, _t(rowptr.astype(np.int32), torch.int32),
                                  _t(idx.astype(np.int16), torch.int16), _t(vals, torch.float32))
     torch.cuda.synchronize()
-    gptr, gidx, gvals = _group_reference(vals, idx, rowptr, V)
+    # the packing drops indices past the map
+    drop = idx >= H * W
+    kept_ptr = np.concatenate([[0], np.cumsum([np.sum(~drop[rowptr[v]:rowptr[v + 1]]) for v in range(V)])])
+    gptr, gidx, gvals = _group_reference(vals[~drop], idx[~drop], kept_ptr, V, hs.GROUP)
     assert np.array_equal(tr.rowptr.cpu().numpy(), gptr)
     assert np.array_equal(tr.idx.cpu().numpy().astype(np.uint16).astype(np.int64)[:gptr[-1]], gidx)
     assert np.array_equal(tr.vals.cpu().numpy().astype(np.float64)[:gptr[-1]], gvals)
     L = f32(oh.forward(sc["light"]))
-    plan = hs.Plan(H, W, 3, max_shifts=4, out_layout=hs.HAAR_LAYOUT_KSC)
+    plan = hs.Plan(H, W, 3, max_shifts=S, out_layout=hs.HAAR_LAYOUT_KSC)
     R = hs.shade_batch(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
     torch.cuda.synchronize()
     Ls = osh.haar_shift(L, H, W, osh.TRANSLATE, sc["params"])
-    ref = osd.radiance(Ls, otr.csr_dense(vals, idx, rowptr, H * W), H, W)
-    assert rel_l2(R.cpu().numpy(), ref) <= 1e-5
+    dense = otr.csr_dense(vals[~drop], idx[~drop], kept_ptr, H * W)
+    ref = osd.radiance(Ls, dense, H, W)
+    Rn = R.cpu().numpy()
+    assert rel_l2(Rn, ref) <= 1e-5
+    assert np.all(Rn[16:32] == 0.0) and np.all(Rn[40:44] == 0.0)
+    assert plan.status() == 0
+    # lighting truncated to its lowest 700 coefficients: stored entries past it contribute nothing
+    K = 700
+    plan_k = hs.Plan(H, W, 3, max_shifts=S, out_coeffs=K, out_layout=hs.HAAR_LAYOUT_KSC)
+    Rk = hs.shade_batch(plan_k, _t(L, torch.float32), _t(sc["params"], torch.float64), tr).cpu().numpy()
+    refk = np.einsum("vk,sck->vsc", dense[:, :K], Ls[..., :K])
+    assert rel_l2(Rk, refk) <= 1e-5
+    assert plan_k.status() == 0
 
 
 def test_csr_full_size_c1_sampled(hs):

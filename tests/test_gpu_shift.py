@@ -59,16 +59,24 @@ def test_translation_matches_oracle(hs, H, W, boundary):
         assert rel_l2(got[s], ref[s]) <= 1e-5, (s, rel_l2(got[s], ref[s]))
 
 
-def test_layouts_and_truncation_agree(hs):
+@pytest.mark.parametrize("C,S", [(3, 3), (3, 17), (4, 13), (1, 50)])
+def test_layouts_and_truncation_agree(hs, C, S):
+    # every layout (and the coefficient-major kernel, with full and partial
+    # plane groups) gives the same bits as the shift-major one
     H, W = 64, 128
-    c = _lighting(3, H, W, 11)
-    prm = np.array([[3.3, 1.7], [100.25, 40.5], [7.0, 0.0]])
+    c = _lighting(C, H, W, 11)
+    rng = np.random.default_rng(S)
+    prm = np.stack([rng.uniform(-W, W, S), rng.uniform(-H, H, S)], axis=1)
+    prm[:3] = [[3.3, 1.7], [100.25, 40.5], [7.0, 0.0]][:S]
     base, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_SCK)
     for lay in (hs.HAAR_LAYOUT_SKC, hs.HAAR_LAYOUT_KSC):
         o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, lay)
         assert np.array_equal(o, base)
-    o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_SCK, K=1000)
-    assert np.array_equal(o, base[..., :1000])
+    for K in (1000, 7):
+        o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_SCK, K=K)
+        assert np.array_equal(o, base[..., :K])
+        o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_KSC, K=K)
+        assert np.array_equal(o, base[..., :K])
 
 
 def test_bf16_hilo_and_f16_outputs(hs):
@@ -90,11 +98,13 @@ def test_bf16_hilo_and_f16_outputs(hs):
 
 @pytest.mark.parametrize("boundary", [SPH, TOR])
 @pytest.mark.parametrize("H,W", [(16, 32), (32, 32), (128, 256)])
-def test_dyadic_shifts_bit_exact(hs, H, W, boundary):
+@pytest.mark.parametrize("layout", [0, 2])
+def test_dyadic_shifts_bit_exact(hs, H, W, boundary, layout):
+    # layout 2 (KSC) runs the coefficient-major kernel
     c = _lighting(2, H, W, 13)
     cases = np.array([[0, 0], [W, 0], [2, 0], [4, 4], [8, 2], [W // 2, H], [16, 2 * H - 16], [6, 10],
                       [64, 32], [-4, -8]], dtype=np.float64)
-    got, _ = _run(hs, c, H, W, 0, cases, boundary)
+    got, _ = _run(hs, c, H, W, 0, cases, boundary, 0, layout)
     for s, (kx, ky) in enumerate(cases.astype(int)):
         per = 2 * H if boundary == SPH else H
         res = osh.dyadic_permutation(c, H, W, int(kx) % W, int(ky) % per, boundary)
@@ -213,3 +223,59 @@ def test_full_size_rotation_c2_hilo(hs):
     for s in (0, 17, 63):
         ref = osh.haar_shift(c, H, W, osh.ROTATE_EULER, sc["params"][s:s + 1], out_coeffs=4096)[0]
         assert rel_l2(got[s], ref) <= ROT_TOL
+
+
+def _run_sampled(hs, coeffs, H, W, kind, params, sample, boundary=SPH):
+    """Full launch of len(params) shifts (FP32, SCK); only the sampled shifts
+    come back to the host."""
+    import torch
+    C = coeffs.shape[0]
+    S = params.shape[0]
+    plan = hs.Plan(H, W, C, kind=kind, boundary=boundary, max_shifts=S)
+    cin = torch.tensor(coeffs, dtype=torch.float32, device="cuda")
+    prm = torch.tensor(np.asarray(params, dtype=np.float64), device="cuda")
+    out = hs.haar_shift(plan, cin, prm)
+    got = out[torch.tensor(sample, device="cuda")].double().cpu().numpy()
+    plan.close()
+    del out
+    return got
+
+
+def test_full_size_translation_batch(hs):
+    # the bench's translation row: 4096 fractional shifts of the RGB 128x256 map in
+    # one launch (three channels per thread); sampled shifts against the oracle
+    sc = synth.scene(1, V=1)
+    H, W = sc["H"], sc["W"]
+    c = f32(oh.forward(sc["light"]))
+    prm = synth.translations(synth.rng_for(1, 7), 4096, 256.0, 256.0)
+    sample = [0, 1, 777, 2048, 4095]
+    got = _run_sampled(hs, c, H, W, 0, prm, sample)
+    ref = osh.haar_shift(c, H, W, osh.TRANSLATE, prm[sample])
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
+
+
+@pytest.mark.parametrize("C,boundary", [(4, SPH), (1, TOR)])
+def test_translation_many_shifts_channel_groups(hs, C, boundary):
+    # enough shifts for the three-channels-per-thread launch, with a partial
+    # channel group (C = 4) and a single channel
+    H, W = 128, 256
+    c = _lighting(C, H, W, 31 + C)
+    rng = np.random.default_rng(C)
+    prm = np.stack([rng.uniform(-2 * W, 2 * W, 320), rng.uniform(-2 * H, 2 * H, 320)], axis=1)
+    prm[5] = [64.0, 32.0]                                     # dyadic: permuted levels
+    sample = [0, 5, 161, 319]
+    got = _run_sampled(hs, c, H, W, 0, prm, sample, boundary)
+    ref = osh.haar_shift(c, H, W, osh.TRANSLATE, prm[sample], boundary)
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
+
+
+def test_full_size_rotation_batch(hs):
+    # the bench's rotation row: 512 rotations of the RGB 256x512 map in one launch
+    sc = synth.scene(2, V=1)
+    H, W = sc["H"], sc["W"]
+    c = f32(oh.forward(sc["light"]))
+    eul = synth.euler_angles(synth.rng_for(2, 7), 512)
+    sample = [0, 300, 511]
+    got = _run_sampled(hs, c, H, W, hs.HAAR_SHIFT_ROTATE_EULER, eul, sample)
+    ref = osh.haar_shift(c, H, W, osh.ROTATE_EULER, eul[sample])
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= ROT_TOL
