@@ -79,6 +79,30 @@ struct haar_shift_plan_s {
 
 namespace hs {
 
+// Programmatic dependent launch: a kernel launched this way may be scheduled
+// while the previous kernel of the stream finishes its last CTAs (which call
+// pdl_trigger() once their outputs are final, or exit); it calls pdl_wait()
+// before it reads anything that kernel wrote.  Without a dependency (first
+// kernel, or a plain launch before it) both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                     cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // status helpers (abi.cu)
 haar_status_t set_error(haar_status_t st, const char* fmt, ...);
 haar_status_t cuda_check(cudaError_t e, const char* what);

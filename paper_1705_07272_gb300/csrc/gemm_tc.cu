@@ -71,6 +71,7 @@ k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
   __syncthreads();
   fence_after();
   const uint32_t tmem = bars.tmem_base;
+  pdl_wait();                                     // set-up above overlaps the kernel that wrote the lighting
 
   if (warp == 0) {
     if (lane == 0) {
@@ -203,8 +204,9 @@ haar_status_t launch_shade_dense_bf16_tc(const __nv_bfloat16* T, int V, int K, c
   const size_t smem = (size_t)stages * stage_bytes + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_dense_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_dense_bf16)");
-  k_dense_bf16<<<grid, THREADS, smem, st>>>(mA, mBh, mBl, V, K, ncols, stages, R, status);
-  return cuda_check(cudaGetLastError(), "k_dense_bf16 launch");
+  return cuda_check(launch_pdl(k_dense_bf16, dim3(grid), dim3(THREADS), smem, st, mA, mBh, mBl, V, K, ncols, stages,
+                              R, status),
+                    "k_dense_bf16 launch");
 }
 
 }  // namespace hs

@@ -18,6 +18,7 @@ namespace hs {
 __global__ void __launch_bounds__(256) k_shade_dense_f32(const float* __restrict__ T, int V, int K,
                                                          const float* __restrict__ L, int ldl, int ncols,
                                                          float* __restrict__ R) {
+  pdl_wait();                                     // inputs come from the previous kernel
   const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= V) return;
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(256) k_shade_csr_f32(const float* __restrict__
                                                        const int32_t* __restrict__ rowptr, int V,
                                                        const float* __restrict__ L, int NL, int ncols,
                                                        float* __restrict__ R) {
+  pdl_wait();                                     // inputs come from the previous kernel
   const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= V) return;
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restri
                                                           int bins, int K, int S, int C,
                                                           const float* __restrict__ L, long long NL,
                                                           float* __restrict__ R) {
+  pdl_wait();                                     // inputs come from the previous kernel
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (long long)V * S) return;
@@ -231,6 +234,7 @@ __global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restri
                                                            const int32_t* __restrict__ gptr, int V,
                                                            const float* __restrict__ L, int NL, int ncols,
                                                            float* __restrict__ R) {
+  pdl_wait();                                     // inputs come from the previous kernel
   typedef unsigned long long u64;
   __shared__ ulonglong2 red[4][4][kGroup][NQ];
   __shared__ float4 sv[8][32];
@@ -505,8 +509,7 @@ __global__ void k_view_bins(int V, int S, int bins, const float* __restrict__ po
 haar_status_t launch_shade_dense_f32(const float* T, int V, int K, const float* L, int ldl, int ncols,
                                      float* R, cudaStream_t st) {
   const long long threads = (long long)V * 32;
-  k_shade_dense_f32<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(T, V, K, L, ldl, ncols, R);
-  return cuda_check(cudaGetLastError(), "k_shade_dense_f32 launch");
+  return cuda_check(launch_pdl(k_shade_dense_f32, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, T, V, K, L, ldl, ncols, R), "k_shade_dense_f32 launch");
 }
 
 haar_status_t launch_shade_csr_f32(const float* vals, const uint16_t* idx, const int32_t* rowptr, int V,
@@ -514,12 +517,13 @@ haar_status_t launch_shade_csr_f32(const float* vals, const uint16_t* idx, const
   const long long threads = (long long)V * 32;
   const unsigned nb = (unsigned)((threads + 255) / 256);
   const int nq = ncols / 4;
-  if (nq <= 4) k_shade_csr_f32<1><<<nb, 256, 0, st>>>(vals, idx, rowptr, V, L, NL, ncols, R);
-  else if (nq <= 8) k_shade_csr_f32<2><<<nb, 256, 0, st>>>(vals, idx, rowptr, V, L, NL, ncols, R);
-  else if (nq <= 12) k_shade_csr_f32<3><<<nb, 256, 0, st>>>(vals, idx, rowptr, V, L, NL, ncols, R);
-  else if (nq <= 16) k_shade_csr_f32<4><<<nb, 256, 0, st>>>(vals, idx, rowptr, V, L, NL, ncols, R);
-  else k_shade_csr_f32<8><<<nb, 256, 0, st>>>(vals, idx, rowptr, V, L, NL, ncols, R);
-  return cuda_check(cudaGetLastError(), "k_shade_csr_f32 launch");
+  cudaError_t e;
+  if (nq <= 4) e = launch_pdl(k_shade_csr_f32<1>, dim3(nb), dim3(256), 0, st, vals, idx, rowptr, V, L, NL, ncols, R);
+  else if (nq <= 8) e = launch_pdl(k_shade_csr_f32<2>, dim3(nb), dim3(256), 0, st, vals, idx, rowptr, V, L, NL, ncols, R);
+  else if (nq <= 12) e = launch_pdl(k_shade_csr_f32<3>, dim3(nb), dim3(256), 0, st, vals, idx, rowptr, V, L, NL, ncols, R);
+  else if (nq <= 16) e = launch_pdl(k_shade_csr_f32<4>, dim3(nb), dim3(256), 0, st, vals, idx, rowptr, V, L, NL, ncols, R);
+  else e = launch_pdl(k_shade_csr_f32<8>, dim3(nb), dim3(256), 0, st, vals, idx, rowptr, V, L, NL, ncols, R);
+  return cuda_check(e, "k_shade_csr_f32 launch");
 }
 
 haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, const int32_t* gptr, int V,
@@ -528,13 +532,14 @@ haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, cons
   const int nq = ncols / 4;
   const long long groups = (V + kGroup - 1) / kGroup;
   const unsigned nb = (unsigned)((groups + 3) / 4);
-  if (nq == 12) k_shade_gcsr_f32<3, true><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else if (nq == 8) k_shade_gcsr_f32<2, true><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else if (nq == 4) k_shade_gcsr_f32<1, true><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else if (nq <= 4) k_shade_gcsr_f32<1, false><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else if (nq <= 8) k_shade_gcsr_f32<2, false><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);
-  else k_shade_gcsr_f32<3, false><<<nb, 256, 0, st>>>(vals, idx, gptr, V, L, NL, ncols, R);   // 48-column passes
-  return cuda_check(cudaGetLastError(), "k_shade_gcsr_f32 launch");
+  cudaError_t e;
+  if (nq == 12) e = launch_pdl(k_shade_gcsr_f32<3, true>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq == 8) e = launch_pdl(k_shade_gcsr_f32<2, true>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq == 4) e = launch_pdl(k_shade_gcsr_f32<1, true>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq <= 4) e = launch_pdl(k_shade_gcsr_f32<1, false>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
+  else if (nq <= 8) e = launch_pdl(k_shade_gcsr_f32<2, false>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
+  else e = launch_pdl(k_shade_gcsr_f32<3, false>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);   // 48-column passes
+  return cuda_check(e, "k_shade_gcsr_f32 launch");
 }
 
 haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16_t* idx, const float* vals,
@@ -556,9 +561,9 @@ haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, c
                                       int V, int bins, int K, int S, int C, const float* L, long long NL,
                                       float* R, cudaStream_t st) {
   const long long threads = (long long)V * S * 32;
-  k_shade_bincsr_f16<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(vals, idx, bin_of, V, bins, K, S, C, L,
-                                                                        NL, R);
-  return cuda_check(cudaGetLastError(), "k_shade_bincsr_f16 launch");
+  return cuda_check(launch_pdl(k_shade_bincsr_f16, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, vals,
+                              idx, bin_of, V, bins, K, S, C, L, NL, R),
+                    "k_shade_bincsr_f16 launch");
 }
 
 haar_status_t launch_view_bins(int V, int S, int bins, const float* pos, const float* nrm,

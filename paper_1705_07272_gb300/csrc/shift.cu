@@ -273,6 +273,7 @@ __device__ __forceinline__ void coarse_levels_warp(const ShiftArgs& a, const Shi
 template <int KIND, int OUT>
 __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   extern __shared__ __align__(16) float smem[];
+  pdl_wait();
   __shared__ int s_last;
   const Geometry& g = a.g;
   const int T = g.T;
@@ -522,6 +523,7 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
   const int c0 = cgrp * CG;
   const int cgn = min(CG, g.C - c0);
   __shared__ ShiftParam s_prm;
+  pdl_wait();
   if (KIND != KIND_COPY && threadIdx.x == 0) s_prm = a.prm[s];
   __syncthreads();
   const ShiftParam* p = (KIND == KIND_COPY) ? nullptr : &s_prm;
@@ -669,6 +671,7 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
     return;
   }
   named_sync(1, nthreads);
+  pdl_trigger();                                  // the tile's levels 1-4 are written
 
   // warp 0: levels 5..Lt on the `groups` values of each channel (a Morton-
   // ordered grid of 16 x 16-pixel blocks)
@@ -751,6 +754,7 @@ __global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int 
   const int plane = p0 + (on ? pl : PG - 1);
   const int s = plane / g.C, c = plane - s * g.C;
   const ShiftParam* pp = a.prm + s;
+  pdl_wait();
   const ShiftParam pr = *pp;
   const int by = morton_y(blk), bx = morton_x(blk);
   const int i0 = tr * 16 + 4 * by, j0 = tc * 16 + 4 * bx;
@@ -841,21 +845,27 @@ __global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int 
   }
   __syncthreads();
 
-  // rows of the group's PG consecutive floats, coefficient by coefficient
+  // rows of the group's PG consecutive floats, one coefficient per warp at a time
   float* out = reinterpret_cast<float*>(a.out);
-  for (int e = t; e < 255 * PG; e += blockDim.x) {
-    const int kl = e / PG, q = e - kl * PG;
-    const int k = ksc_global_k(g, kl, tr, tc);
-    if (k < a.K) out[(long long)k * P + p0 + q] = stage[kl * kKscPitch + q];
+  for (int kl = t >> 5; kl < 255; kl += blockDim.x >> 5) {
+    const int k = ksc_global_k(g, kl, tr, tc);                // warp-uniform
+    if (k < a.K) {
+      float* orow = out + (long long)k * P + p0;
+      const float* srow = stage + kl * kKscPitch;
+      for (int q = lane; q < PG; q += 32) orow[q] = srow[q];
+    }
   }
 
+  pdl_trigger();                                  // the tile's rows are written
+  // the tile means were published (stores + fence by their writers) before
+  // the barrier above; thread 0 counts the tile and, last, acquires them all
   if (t == 0) {
     const unsigned n = atomicAdd(a.counters + blockIdx.y, 1u);
     s_last = (n == (unsigned)(g.n_tiles - 1)) ? 1 : 0;
+    if (s_last) __threadfence();
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   // coarse levels of every plane of the group, 16 threads per plane; both
   // images start on 16-byte boundaries (the passes read them as float4)
   const int nt4 = (g.n_tiles + 3) & ~3;
@@ -909,6 +919,7 @@ __device__ __forceinline__ float synth_pixel(const float* cf, int i, int j, int 
 }
 
 __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
+  pdl_trigger();                                  // the shift kernel may be scheduled (it waits for this grid)
   const long long N = (long long)a.H * a.W;
   if ((int)blockIdx.x < a.nbp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1032,8 +1043,7 @@ static haar_status_t launch_reg(const ShiftArgs& a, int S, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_reg)");
   }
   dim3 grid(a.g.n_tiles, S, (a.g.C + CG - 1) / CG);
-  fr<<<grid, nb * nb, sm, st>>>(a);
-  return cuda_check(cudaGetLastError(), "k_shift_reg launch");
+  return cuda_check(launch_pdl(fr, grid, dim3(nb * nb), sm, st, a), "k_shift_reg launch");
 }
 
 // Channels per thread: a rotation shares its coordinates across kRotChannels
@@ -1060,8 +1070,7 @@ static haar_status_t launch_k(const ShiftArgs& a, int S, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift)");
   }
   dim3 grid(a.g.n_tiles, S, (a.g.C + CG - 1) / CG);
-  fn<<<grid, kThreads, sm, st>>>(a);
-  return cuda_check(cudaGetLastError(), "k_shift launch");
+  return cuda_check(launch_pdl(fn, grid, dim3(kThreads), sm, st, a), "k_shift launch");
 }
 
 template <int KIND>
@@ -1142,8 +1151,7 @@ static haar_status_t launch_ksc(haar_shift_plan_s* p, const float* coeffs_in, in
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_ksc)");
   }
   dim3 grid(g.n_tiles, (unsigned)((P + kKscPlanes - 1) / kKscPlanes));
-  k_shift_ksc<<<grid, 16 * kKscPlanes, sm, st>>>(a, (int)P);
-  return cuda_check(cudaGetLastError(), "k_shift_ksc launch");
+  return cuda_check(launch_pdl(k_shift_ksc, grid, dim3(16 * kKscPlanes), sm, st, a, (int)P), "k_shift_ksc launch");
 }
 
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
