@@ -217,8 +217,8 @@ __device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 6
 // CTA = 4 groups x 2 warps (a pair per group; the two warps split the
 // group's union list in halves and add through shared memory, a named
 // barrier per pair).  A warp takes 8 entries per step: lane
-// = 4 e + cq, entry slot e, column quarter cq (NQ float4 of the lighting
-// row), and accumulates its columns for the 4 vertices with paired FMAs;
+// = 4 e + cq, entry slot e, float4 columns cq, cq + 4, ... (NQ of the
+// lighting row), and accumulates its columns for the 4 vertices with paired FMAs;
 // the 8 slots are summed with shuffles at the end.  The union list streams
 // in batches of 32 (indices kept in a register, values staged in shared
 // memory), the next batch requested while the current one is used, the
@@ -257,11 +257,13 @@ __global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restri
       if (ie > ib) l2_prefetch_bulk(reinterpret_cast<const void*>(ib), (unsigned)(ie - ib));
     }
     for (int q0 = 0; q0 < nq; q0 += 4 * NQ) {
-      const int qb = q0 + cq * NQ;
-      // columns beyond the row (generic widths only) read row 0's first float4 and are not stored
+      // lane cq takes float4 columns q0 + cq + 4 m: each load instruction then
+      // reads 64 contiguous bytes of a row (2 sectors), a row costs its 6
+      // sectors once; columns beyond the row (generic widths only) read row
+      // 0's first float4 and are not stored
       int qoff[NQ];
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) qoff[m] = (EXACT || qb + m < nq) ? qb + m : 0;
+      for (int m = 0; m < NQ; ++m) qoff[m] = (EXACT || q0 + cq + 4 * m < nq) ? q0 + cq + 4 * m : 0;
       u64 acc[kGroup][NQ][2];
 #pragma unroll
       for (int v = 0; v < kGroup; ++v)
@@ -347,10 +349,10 @@ __global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restri
           if (vv < V) {
 #pragma unroll
             for (int m = 0; m < NQ; ++m) {
-              if (EXACT || qb + m < nq) {
+              if (EXACT || q0 + cq + 4 * m < nq) {
                 const ulonglong2 o = red[gl][cq][v][m];
                 const u64 s0 = f2_add(acc[v][m][0], o.x), s1 = f2_add(acc[v][m][1], o.y);
-                reinterpret_cast<ulonglong2*>(R + (long long)vv * ncols)[qb + m] = make_ulonglong2(s0, s1);
+                reinterpret_cast<ulonglong2*>(R + (long long)vv * ncols)[q0 + cq + 4 * m] = make_ulonglong2(s0, s1);
               }
             }
           }
