@@ -15,6 +15,14 @@ optimization").
 integer shift does to the levels whose block side divides it: it moves whole
 blocks, so those coefficients are a signed permutation of the input.
 
+``start_level`` k > 0 is the paper's start-level approximation (Sec.
+"Algorithmic optimization": the shift can begin at a coarser level, with
+O(N / 4^k) work): the coarsest N / 4^k coefficients of the map are those of
+its level-k scaling image (an (H / 2^k) x (W / 2^k) map whose pixels are
+2^k x the 2^k x 2^k block means), so the shift is taken of that image -- a
+translation by (dx, dy) / 2^k, a rotation unchanged -- and gives the N / 4^k
+coarsest coefficients; the finer ones are not produced.
+
 Test infrastructure only (see the package docstring).
 """
 from __future__ import annotations
@@ -45,9 +53,19 @@ def shifted_maps(P: np.ndarray, kind: int, params: np.ndarray, boundary: int) ->
 
 
 def haar_shift(coeffs: np.ndarray, H: int, W: int, kind: int, params: np.ndarray,
-               boundary: int = SPHERE, out_coeffs: int | None = None) -> np.ndarray:
-    """Shifted coefficients [S, C, K] of coefficients [C, N] (float64)."""
+               boundary: int = SPHERE, out_coeffs: int | None = None, start_level: int = 0) -> np.ndarray:
+    """Shifted coefficients [S, C, K] of coefficients [C, N] (float64).
+
+    start_level k: the shift of the level-k scaling image (see the module
+    docstring); K <= N / 4^k."""
     c = np.asarray(coeffs, dtype=np.float64)
+    k = int(start_level)
+    if k:
+        H, W = H >> k, W >> k
+        c = c[..., :H * W]                      # the scaling image's own coefficients
+        params = np.asarray(params, dtype=np.float64)
+        if kind == TRANSLATE:
+            params = params / float(1 << k)
     P = haar.inverse(c, H, W)
     G = shifted_maps(P, kind, params, boundary)
     out = haar.forward(G)

@@ -218,3 +218,62 @@ def test_translation_by_bilinear_equals_area_projection():
                     acc += (a1 - a0) * (b1 - b0) * P[si % H, sj % W]
             ref[i, j] = acc
     assert np.abs(g - ref).max() < 1e-12
+
+
+# ---------------------------------------------------------------- start level
+
+def _block_image(P, k):
+    """2^k x (mean over each 2^k x 2^k block): the level-k scaling image in pixel form."""
+    H, W = P.shape[-2:]
+    b = 1 << k
+    return P.reshape(P.shape[:-2] + (H // b, b, W // b, b)).mean(axis=(-3, -1)) * b
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_start_level_is_the_shift_of_the_block_mean_image(k):
+    # the N / 4^k coarsest coefficients are those of the 2^k-scaled block-mean
+    # image, built here from pixels, not from coefficients
+    H, W = 32, 64
+    rng = np.random.default_rng(k)
+    P = rng.lognormal(0.0, 1.0, (2, H, W))
+    c = haar.forward(P)
+    assert np.allclose(c[:, :(H * W) >> (2 * k)], haar.forward(_block_image(P, k)), rtol=0, atol=1e-12)
+    prm = np.array([[3.25, 1.5], [100.7, -40.2]])
+    got = shift.haar_shift(c, H, W, TR, prm, start_level=k)
+    Pb = _block_image(P, k)
+    ref = np.stack([haar.forward(resample.translate(Pb, dx / (1 << k), dy / (1 << k), SPHERE)) for dx, dy in prm])
+    assert got.shape == (2, 2, (H * W) >> (2 * k))
+    assert np.allclose(got, ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("boundary", [SPHERE, TORUS])
+@pytest.mark.parametrize("k", [1, 2])
+def test_start_level_exact_for_block_aligned_shifts(k, boundary):
+    # whole-block moves commute with block averaging: the start-level result is
+    # then the exact shift's coarsest N / 4^k coefficients
+    H, W = 32, 64
+    rng = np.random.default_rng(10 + k)
+    c = haar.forward(rng.lognormal(0.0, 1.0, (3, H, W)))
+    b = 1 << k
+    prm = np.array([[b, 0], [3 * b, 5 * b], [W - b, 2 * H - 2 * b], [0, 7 * b]], dtype=np.float64)
+    exact = shift.haar_shift(c, H, W, TR, prm, boundary)
+    got = shift.haar_shift(c, H, W, TR, prm, boundary, start_level=k)
+    n = (H * W) >> (2 * k)
+    assert np.allclose(got, exact[..., :n], rtol=0, atol=1e-10)
+    # a fractional shift is only approximated at the start level
+    frac = shift.haar_shift(c, H, W, TR, np.array([[0.5 * b, 0.25 * b]]), boundary, start_level=k)
+    full = shift.haar_shift(c, H, W, TR, np.array([[0.5 * b, 0.25 * b]]), boundary)[..., :n]
+    assert not np.allclose(frac, full, atol=1e-6)
+
+
+def test_start_level_rotation_identity_and_constants():
+    H, W = 32, 64
+    rng = np.random.default_rng(5)
+    c = haar.forward(rng.lognormal(0.0, 1.0, (1, H, W)))
+    for k in (1, 2):
+        n = (H * W) >> (2 * k)
+        got = shift.haar_shift(c, H, W, shift.ROTATE_EULER, np.zeros((1, 3)), start_level=k)
+        assert np.allclose(got[0], c[:, :n], rtol=0, atol=1e-10)
+        const = haar.forward(np.full((1, H, W), 2.5))
+        rot = shift.haar_shift(const, H, W, shift.ROTATE_EULER, np.array([[0.3, 1.1, -2.0]]), start_level=k)
+        assert np.allclose(rot[0], const[:, :n], rtol=0, atol=1e-10)
