@@ -101,6 +101,13 @@ typedef struct {
   int out_coeffs; /* K: the K lowest canonical coefficients are written (0 = all) */
   int out_type;   /* haar_out_t */
   int out_layout; /* haar_layout_t */
+  int start_level; /* k >= 0, H >> k >= 2: the shift starts at level k (Sec. "Algorithmic
+                      optimization"): it is taken of the level-k scaling image, the
+                      (H/2^k) x (W/2^k) map of 2^k x the 2^k x 2^k block means, whose
+                      coefficients are the N/4^k coarsest of coeffs_in; a translation
+                      moves it by (dx, dy)/2^k, a rotation is unchanged.  Only those
+                      N/4^k coefficients are produced (K <= N/4^k; out_coeffs = 0 means
+                      all of them), for O(N/4^k) work.  0 = the full map. */
 } haar_shift_desc_t;
 
 /* Create a plan: validates the descriptor and allocates its device workspace

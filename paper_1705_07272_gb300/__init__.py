@@ -57,7 +57,8 @@ EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_for
 class HaarShiftDesc(ctypes.Structure):
     _fields_ = [("height", ctypes.c_int), ("width", ctypes.c_int), ("channels", ctypes.c_int),
                 ("kind", ctypes.c_int), ("boundary", ctypes.c_int), ("max_shifts", ctypes.c_int),
-                ("out_coeffs", ctypes.c_int), ("out_type", ctypes.c_int), ("out_layout", ctypes.c_int)]
+                ("out_coeffs", ctypes.c_int), ("out_type", ctypes.c_int), ("out_layout", ctypes.c_int),
+                ("start_level", ctypes.c_int)]
 
 
 class HaarTransportDesc(ctypes.Structure):
@@ -163,15 +164,16 @@ class Plan:
     """A haar_shift_plan_t and its descriptor."""
 
     def __init__(self, height, width, channels, kind=HAAR_SHIFT_TRANSLATE, boundary=HAAR_BOUNDARY_SPHERE,
-                 max_shifts=1, out_coeffs=0, out_type=HAAR_OUT_F32, out_layout=HAAR_LAYOUT_SCK):
+                 max_shifts=1, out_coeffs=0, out_type=HAAR_OUT_F32, out_layout=HAAR_LAYOUT_SCK, start_level=0):
         self.desc = HaarShiftDesc(height, width, channels, kind, boundary, max_shifts, out_coeffs,
-                                  out_type, out_layout)
+                                  out_type, out_layout, start_level)
         h = ctypes.c_void_p()
         _check(lib().haar_shift_plan(ctypes.byref(self.desc), ctypes.byref(h)))
         self.handle = h.value
         self.H, self.W, self.C = height, width, channels
         self.N = height * width
-        self.K = out_coeffs or self.N
+        self.start_level = start_level
+        self.K = out_coeffs or (self.N >> (2 * start_level))
         self.kind, self.out_type, self.out_layout = kind, out_type, out_layout
 
     def close(self):

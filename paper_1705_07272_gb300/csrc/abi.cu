@@ -89,7 +89,11 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: unknown boundary %d", d->boundary);
   if (d->max_shifts < 1 || d->max_shifts > 65535)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: max_shifts %d not in [1, 65535]", d->max_shifts);
-  const long long N = (long long)d->height * d->width;
+  if (d->start_level < 0 || (d->height >> d->start_level) < 2)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: start_level %d leaves a map smaller than 2 x 2",
+                     d->start_level);
+  const int Hk = d->height >> d->start_level, Wk = d->width >> d->start_level;
+  const long long N = (long long)Hk * Wk;          // coefficients of the map the shift runs on
   if (d->out_coeffs < 0 || d->out_coeffs > N)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: out_coeffs %d not in [0, %lld]", d->out_coeffs, N);
   if (d->out_type < HAAR_OUT_F32 || d->out_type > HAAR_OUT_F16)
@@ -101,9 +105,10 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
   if (!p) return set_error(HAAR_ERR_NOMEM, "haar_shift_plan: host allocation failed");
   memset(p, 0, sizeof(*p));
   p->desc = *d;
-  p->geo = make_geometry(d->height, d->width, d->channels, d->boundary,
-                         choose_tile(d->height, d->width, d->channels, d->max_shifts));
+  p->geo = make_geometry(Hk, Wk, d->channels, d->boundary, choose_tile(Hk, Wk, d->channels, d->max_shifts));
   p->K = d->out_coeffs ? d->out_coeffs : (int)N;
+  p->cin_stride = (long long)d->height * d->width;
+  p->pscale = 1.0 / (double)(1 << d->start_level);
   cudaGetDevice(&p->device);
   const Geometry& g = p->geo;
   const size_t S = d->max_shifts;
@@ -115,8 +120,8 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
   if (e == cudaSuccess) e = cudaMalloc(&p->trig, sizeof(float) * 2 * (g.H + g.W));
   if (e == cudaSuccess) e = cudaMalloc(&p->prm, sizeof(ShiftParam) * S);
   p->means_cap = S * g.C * g.n_tiles;
-  if (ksc_eligible(*d, (int)S) && ksc_means_floats(*d, (int)S) > p->means_cap)
-    p->means_cap = ksc_means_floats(*d, (int)S);
+  if (ksc_eligible(*d, g, (int)S) && ksc_means_floats(g, (int)S) > p->means_cap)
+    p->means_cap = ksc_means_floats(g, (int)S);
   if (e == cudaSuccess) e = cudaMalloc(&p->means, sizeof(float) * p->means_cap);
   if (e == cudaSuccess) e = cudaMalloc(&p->counters, sizeof(unsigned) * S);
   if (e == cudaSuccess) e = cudaMalloc(&p->light, light_bytes);

@@ -62,8 +62,10 @@ static inline Geometry make_geometry(int H, int W, int C, int boundary, int tile
 
 struct haar_shift_plan_s {
   haar_shift_desc_t desc;
-  hs::Geometry geo;
+  hs::Geometry geo;          // of the map the shift runs on (the level-k scaling image for start_level k)
   int K;                     // coefficients written per (s, c)
+  long long cin_stride;      // floats between the channels of coeffs_in (the full map's N)
+  double pscale;             // translation scale 2^-start_level
   int device;
   // workspace (device)
   float* pix;                // [C][H][W] pixel map synthesised per launch
@@ -114,8 +116,8 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
                            cudaStream_t st);
 haar_status_t launch_trig(haar_shift_plan_s* p, cudaStream_t st);
-bool ksc_eligible(const haar_shift_desc_t& d, int S);
-size_t ksc_means_floats(const haar_shift_desc_t& d, int S);
+bool ksc_eligible(const haar_shift_desc_t& d, const Geometry& g, int S);
+size_t ksc_means_floats(const Geometry& g, int S);
 size_t ksc_smem_floats(long long n16);
 haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* coeffs,
                              float scale, cudaStream_t st);

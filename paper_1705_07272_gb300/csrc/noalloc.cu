@@ -37,9 +37,14 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   if (injected("haar_shift_noalloc")) return set_error(HAAR_ERR_INJECTED, "haar_shift_noalloc: injected fault");
   if (d == nullptr || cin == nullptr || params == nullptr || out == nullptr)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: null argument");
-  const int H = d->height, W = d->width, C = d->channels;
-  if (H < 2 || H > 4096 || (H & (H - 1)) != 0 || (W != H && W != 2 * H))
-    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: unsupported map %dx%d", H, W);
+  const int C = d->channels;
+  if (d->height < 2 || d->height > 4096 || (d->height & (d->height - 1)) != 0 ||
+      (d->width != d->height && d->width != 2 * d->height))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: unsupported map %dx%d", d->height, d->width);
+  if (d->start_level < 0 || (d->height >> d->start_level) < 2)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: start_level %d leaves a map smaller than 2 x 2",
+                     d->start_level);
+  const int H = d->height >> d->start_level, W = d->width >> d->start_level;   // the map the shift runs on
   if (C < 1 || C > 64) return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: channels %d not in [1, 64]", C);
   if (d->kind < HAAR_SHIFT_TRANSLATE || d->kind > HAAR_SHIFT_ROTATE_EULER ||
       (d->boundary != HAAR_BOUNDARY_SPHERE && d->boundary != HAAR_BOUNDARY_TORUS) ||
@@ -60,7 +65,7 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   const size_t n_trig = round64(2 * (size_t)(H + W));
   const size_t n_prm = round64((size_t)S * sizeof(ShiftParam) / sizeof(float));
   size_t n_means = round64((size_t)S * C * g.n_tiles);
-  if (ksc_eligible(*d, S) && round64(ksc_means_floats(*d, S)) > n_means) n_means = round64(ksc_means_floats(*d, S));
+  if (ksc_eligible(*d, g, S) && round64(ksc_means_floats(g, S)) > n_means) n_means = round64(ksc_means_floats(g, S));
   const size_t n_cnt = round64((size_t)S);
   const size_t need = n_pix + n_trig + n_prm + n_means + n_cnt;
   if (need > kNoAllocFloats)
@@ -91,6 +96,8 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   p.desc.max_shifts = S;
   p.geo = g;
   p.K = d->out_coeffs ? d->out_coeffs : (int)N;
+  p.cin_stride = (long long)d->height * d->width;
+  p.pscale = 1.0 / (double)(1 << d->start_level);
   p.device = dev;
   p.pix = base;
   p.trig = base + n_pix;

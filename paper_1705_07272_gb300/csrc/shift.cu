@@ -32,7 +32,8 @@ struct ShiftArgs {
   long long plane;        // hi -> lo plane offset (BF16_HILO)
   void* out;
   const float* pix;       // source pixels [C][H][W] (or maps [batch][H][W] for KIND_COPY)
-  const float* cin;       // input coefficients [C][N] (signed-permutation copies)
+  const float* cin;       // input coefficients [C][cin_stride] (signed-permutation copies)
+  long long cin_stride;
   const ShiftParam* prm;  // [S] or null
   float* means;           // [S][C][n_tiles] (null: means go to out[..., 0:n_tiles])
   unsigned* counters;     // [S] (null: no in-kernel coarse pass)
@@ -99,7 +100,7 @@ __device__ float perm_value(const ShiftArgs& a, const ShiftParam& p, int c, int 
   }
   cs %= cols;
   if (cs < 0) cs += cols;
-  const float* src = a.cin + (long long)c * g.N;
+  const float* src = a.cin + (long long)c * a.cin_stride;
   if (lvl > g.n) return __ldg(src + cs);
   const long long gl = (long long)g.q << (2 * (g.n - l));
   float v = __ldg(src + gl * (1 + band) + (long long)rs * cols + cs);
@@ -898,6 +899,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_inplace(ShiftArgs a) {
 // per-shift tile counters.
 struct SetupArgs {
   int H, W, C, n, q, kind, boundary, S, nbp;
+  long long cin_stride;   // floats between input channels (the full map's N)
+  double pscale;          // translation scale (2^-start_level)
   const float* cin;
   float* pix;
   const double* params;
@@ -927,7 +930,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
     const int c = (int)(e / N);
     const long long rem = e - (long long)c * N;
     const int i = (int)(rem / a.W), j = (int)(rem - (long long)i * a.W);
-    a.pix[e] = synth_pixel(a.cin + (long long)c * N, i, j, a.W, a.n, a.q);
+    a.pix[e] = synth_pixel(a.cin + (long long)c * a.cin_stride, i, j, a.W, a.n, a.q);
     return;
   }
   for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
@@ -940,7 +943,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
     for (int k = 0; k < 9; ++k) p.R[k] = (k % 4 == 0) ? 1.0f : 0.0f;
     p.pad2[0] = p.pad2[1] = p.pad2[2] = 0.0f;
     if (a.kind == HAAR_SHIFT_TRANSLATE) {
-      const double dx = a.params[2 * s], dy = a.params[2 * s + 1];
+      const double dx = a.params[2 * s] * a.pscale, dy = a.params[2 * s + 1] * a.pscale;
       const double W = a.W;
       const double per = (a.boundary == HAAR_BOUNDARY_SPHERE) ? 2.0 * a.H : (double)a.H;
       double x = dx - W * floor(dx / W);
@@ -1099,6 +1102,8 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
   const long long total = g.N * g.C;
   a.nbp = (int)((total + kThreads - 1) / kThreads);
   a.cin = coeffs_in;
+  a.cin_stride = p->cin_stride;
+  a.pscale = p->pscale;
   a.pix = p->pix;
   a.params = params;
   a.prm = p->prm;
@@ -1109,17 +1114,17 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
 
 // The coefficient-major kernel serves F32 KSC translations whose tile-mean
 // workspace and shared-memory coarse pass fit.
-bool ksc_eligible(const haar_shift_desc_t& d, int S) {
+bool ksc_eligible(const haar_shift_desc_t& d, const Geometry& g, int S) {
   if (d.kind != HAAR_SHIFT_TRANSLATE || d.out_type != HAAR_OUT_F32 || d.out_layout != HAAR_LAYOUT_KSC) return false;
-  if (d.height < 16) return false;
-  const long long P = (long long)S * d.channels;
+  if (g.H < 16) return false;
+  const long long P = (long long)S * g.C;
   if ((P + kKscPlanes - 1) / kKscPlanes > S) return false;                 // one counter per plane group
-  const long long n16 = (long long)(d.height / 16) * (d.width / 16);
+  const long long n16 = (long long)(g.H / 16) * (g.W / 16);
   return ksc_smem_floats(n16) * sizeof(float) <= 200 * 1024;
 }
 
-size_t ksc_means_floats(const haar_shift_desc_t& d, int S) {
-  return (size_t)S * d.channels * (size_t)(d.height / 16) * (d.width / 16);
+size_t ksc_means_floats(const Geometry& g, int S) {
+  return (size_t)S * g.C * (size_t)(g.H / 16) * (g.W / 16);
 }
 
 size_t ksc_smem_floats(long long n16) {
@@ -1139,6 +1144,7 @@ static haar_status_t launch_ksc(haar_shift_plan_s* p, const float* coeffs_in, in
   a.out = out;
   a.pix = p->pix;
   a.cin = coeffs_in;
+  a.cin_stride = p->cin_stride;
   a.prm = p->prm;
   a.means = p->means;
   a.counters = p->counters;
@@ -1156,7 +1162,7 @@ static haar_status_t launch_ksc(haar_shift_plan_s* p, const float* coeffs_in, in
 
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
                            cudaStream_t st) {
-  if (ksc_eligible(p->desc, S) && ksc_means_floats(p->desc, S) <= p->means_cap)
+  if (ksc_eligible(p->desc, p->geo, S) && ksc_means_floats(p->geo, S) <= p->means_cap)
     return launch_ksc(p, coeffs_in, S, out, st);
   ShiftArgs a;
   const Geometry& g = p->geo;
@@ -1172,6 +1178,7 @@ haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, 
   a.out = out;
   a.pix = p->pix;
   a.cin = coeffs_in;
+  a.cin_stride = p->cin_stride;
   a.prm = p->prm;
   a.means = p->means;
   a.counters = p->counters;
@@ -1195,6 +1202,7 @@ haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* 
   a.out = coeffs;
   a.pix = maps;
   a.cin = nullptr;
+  a.cin_stride = 0;
   a.prm = nullptr;
   a.means = nullptr;
   a.counters = nullptr;

@@ -41,7 +41,7 @@ def test_version(lib):
 
 def _desc(lib, **kw):
     d = dict(height=32, width=64, channels=3, kind=0, boundary=0, max_shifts=4, out_coeffs=0,
-             out_type=0, out_layout=0)
+             out_type=0, out_layout=0, start_level=0)
     d.update(kw)
     return lib.HaarShiftDesc(**d)
 
@@ -49,7 +49,9 @@ def _desc(lib, **kw):
 @pytest.mark.parametrize("bad", [dict(height=48), dict(height=1), dict(width=128), dict(width=16),
                                  dict(channels=0), dict(channels=65), dict(kind=7), dict(boundary=2),
                                  dict(max_shifts=0), dict(out_coeffs=-1), dict(out_coeffs=32 * 64 + 1),
-                                 dict(out_type=3), dict(out_layout=5), dict(height=8192, width=8192)])
+                                 dict(out_type=3), dict(out_layout=5), dict(height=8192, width=8192),
+                                 dict(start_level=-1), dict(start_level=5),
+                                 dict(start_level=2, out_coeffs=(32 * 64 >> 4) + 1)])
 def test_plan_rejects_bad_descriptors(lib, bad):
     h = ctypes.c_void_p()
     st = lib.lib().haar_shift_plan(ctypes.byref(_desc(lib, **bad)), ctypes.byref(h))

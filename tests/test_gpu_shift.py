@@ -22,12 +22,12 @@ def _lighting(C, H, W, seed):
     return f32(oh.forward(synth.lighting_pixels(rng, C, H, W)))
 
 
-def _run(hs, coeffs, H, W, kind, params, boundary=SPH, out_type=0, layout=0, K=0):
+def _run(hs, coeffs, H, W, kind, params, boundary=SPH, out_type=0, layout=0, K=0, start_level=0):
     import torch
     C = coeffs.shape[0]
     S = params.shape[0]
     plan = hs.Plan(H, W, C, kind=kind, boundary=boundary, max_shifts=S, out_coeffs=K,
-                   out_type=out_type, out_layout=layout)
+                   out_type=out_type, out_layout=layout, start_level=start_level)
     cin = torch.tensor(coeffs, dtype=torch.float32, device="cuda")
     prm = torch.tensor(np.asarray(params, dtype=np.float64), device="cuda")
     out = hs.haar_shift(plan, cin, prm)
@@ -278,4 +278,41 @@ def test_full_size_rotation_batch(hs):
     sample = [0, 300, 511]
     got = _run_sampled(hs, c, H, W, hs.HAAR_SHIFT_ROTATE_EULER, eul, sample)
     ref = osh.haar_shift(c, H, W, osh.ROTATE_EULER, eul[sample])
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= ROT_TOL
+
+
+@pytest.mark.parametrize("k,layout", [(1, 0), (2, 0), (1, 2), (3, 2)])
+def test_start_level_translation_matches_oracle(hs, k, layout):
+    # the shift of the level-k scaling image of the RGB 128x256 map (Sec.
+    # "Algorithmic optimization"); layout 2 (KSC) runs the coefficient-major kernel
+    sc = synth.scene(1, V=1)
+    H, W = sc["H"], sc["W"]
+    c = f32(oh.forward(sc["light"]))
+    prm = np.asarray(sc["params"], dtype=np.float64)
+    prm[1] = [64.0, 32.0]                                     # block-aligned at every k used here
+    import torch
+    plan = hs.Plan(H, W, 3, max_shifts=len(prm), out_layout=layout, start_level=k)
+    out = hs.haar_shift(plan, torch.tensor(c, dtype=torch.float32, device="cuda"),
+                        torch.tensor(prm, dtype=torch.float64, device="cuda"))
+    got = out.double().cpu().numpy()
+    if layout == hs.HAAR_LAYOUT_KSC:
+        got = got.transpose(1, 2, 0)
+    plan.close()
+    n = (H * W) >> (2 * k)
+    assert got.shape == (len(prm), 3, n)
+    ref = osh.haar_shift(c, H, W, osh.TRANSLATE, prm, start_level=k)
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
+    # block-aligned shifts: the start level is exact, against the full-map shift
+    full = osh.haar_shift(c, H, W, osh.TRANSLATE, prm[1:2])[0, :, :n]
+    assert rel_l2(got[1], full) <= 1e-5
+
+
+def test_start_level_rotation_matches_oracle(hs):
+    sc = synth.scene(2, V=1)
+    H, W = sc["H"], sc["W"]
+    c = f32(oh.forward(sc["light"]))
+    eul = np.asarray(sc["params"][:8], dtype=np.float64)
+    got, _ = _run(hs, c, H, W, hs.HAAR_SHIFT_ROTATE_EULER, eul, SPH, 0, 0, K=0, start_level=1)
+    ref = osh.haar_shift(c, H, W, osh.ROTATE_EULER, eul, start_level=1)
+    assert got.shape == ref.shape == (8, 3, (H * W) >> 2)
     assert rel_l2(got, ref, axis=(1, 2)).max() <= ROT_TOL

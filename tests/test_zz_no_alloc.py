@@ -29,14 +29,17 @@ def test_noalloc_matches_plan_shift_twice(hs):
         (64, 128, 3, hs.HAAR_SHIFT_TRANSLATE, hs.HAAR_LAYOUT_KSC, np.array([[3.3, 1.7], [100.25, 40.5], [8.0, 4.0]])),
         (32, 64, 3, hs.HAAR_SHIFT_ROTATE_EULER, hs.HAAR_LAYOUT_SCK, synth.euler_angles(np.random.default_rng(1), 4)),
     ]
-    for H, W, C, kind, layout, prm in cases:
+    cases.append((128, 256, 3, hs.HAAR_SHIFT_TRANSLATE, hs.HAAR_LAYOUT_KSC, np.array([[5.5, 2.25], [40.0, 16.0]]), 2))
+    for case in cases:
+        H, W, C, kind, layout, prm = case[:6]
+        k = case[6] if len(case) > 6 else 0
         rng = np.random.default_rng(H)
         c = f32(oh.forward(synth.lighting_pixels(rng, C, H, W)))
         cin = torch.tensor(c, dtype=torch.float32, device="cuda")
         params = torch.tensor(prm, dtype=torch.float64, device="cuda")
-        plan = hs.Plan(H, W, C, kind=kind, max_shifts=len(prm), out_layout=layout)
+        plan = hs.Plan(H, W, C, kind=kind, max_shifts=len(prm), out_layout=layout, start_level=k)
         ref = hs.haar_shift(plan, cin, params)
-        desc = hs.HaarShiftDesc(H, W, C, kind, 0, len(prm), 0, 0, layout)
+        desc = hs.HaarShiftDesc(H, W, C, kind, 0, len(prm), 0, 0, layout, k)
         for _ in range(2):
             out = torch.full_like(ref, float("nan"))
             assert _noalloc(hs, desc, cin, params, out) == hs.HAAR_OK, hs.lib().haar_last_error()
