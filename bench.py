@@ -290,6 +290,29 @@ def measure_rows(hs, dev, flush, only=None):
         plan.close()
         del out
 
+    # start-level sweep (the paper's accuracy / cost knob): the 64 c2 rotations of
+    # RGB 256x512 started at level k = 0..3, time and rel-L2 of the N/4^k
+    # coarsest coefficients against the full-map shift's
+    if want("start_level_sweep"):
+        sc2 = synth.scene(2, V=1)
+        L2 = hs.haar_forward(torch.tensor(sc2["light"], dtype=torch.float32, device=dev))
+        eul = torch.tensor(sc2["params"], dtype=torch.float64, device=dev)
+        S = eul.shape[0]
+        sweep, exact = [], None
+        for k in range(4):
+            plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, start_level=k)
+            out = torch.empty(plan.out_shape(S), dtype=torch.float32, device=dev)
+            ms = _timeit(lambda: hs.haar_shift(plan, L2, eul, out), 10, flush, stream)
+            if k == 0:
+                exact = out.clone()
+            n = out.shape[-1]
+            ref = exact[..., :n]
+            err = float(((out - ref).norm() / ref.norm()).item())
+            sweep.append({"start_level": k, "coeffs": n, "ms": ms, "rel_l2_vs_full_map": err})
+            plan.close()
+        rows["start_level_sweep"] = {"what": "64 rotations of RGB 256x512 started at level k (Sec. Algorithmic "
+                                             "optimization), FP32", "levels": sweep}
+
     # c2 frame: 64 rotations -> bf16 hi/lo lowest 4096 -> tcgen05 contraction for 200k vertices
     if want("c2_dense_tc"):
         sc2 = synth.scene(2)

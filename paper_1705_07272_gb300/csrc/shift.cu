@@ -44,6 +44,28 @@ struct ShiftArgs {
 
 // ------------------------------------------------------------------ helpers
 
+// atan2(y, x) in [-pi, pi] for the rotation coordinates: reduction to
+// t = min(|x|, |y|) / max(|x|, |y|) in [0, 1], atan(t) = t P(t^2) with P of
+// degree 7 (coefficients from a least-squares fit on [0, 1] reweighted
+// towards its largest errors: |error| < 1.5e-7 rad when evaluated in FP32,
+// i.e. < 2e-5 pixel at 512 columns), then the reflections atan(y/x) =
+// pi/2 - atan(x/y) and the half-plane x < 0.  (0, 0) gives 0.
+__device__ __forceinline__ float rot_atan2(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  const float t = (mx > 0.0f) ? __fdividef(mn, mx) : 0.0f;
+  const float u = t * t;
+  constexpr float P[8] = {9.999993443e-01f, -3.332985938e-01f, 1.994656622e-01f, -1.390863210e-01f, 9.642205387e-02f, -5.591243505e-02f, 2.186303213e-02f, -4.054587334e-03f};
+  float p = P[7];
+#pragma unroll
+  for (int i = 6; i >= 0; --i) p = fmaf(p, u, P[i]);
+  float r = t * p;
+  if (ay > ax) r = 1.57079632679f - r;
+  if (x < 0.0f) r = 3.14159265359f - r;
+  return copysignf(r, y);
+}
+
+
 __device__ __forceinline__ void ext_index(int& i, int& j, int H, int W, int boundary) {
   if (boundary == HAAR_BOUNDARY_TORUS) {
     i %= H;
@@ -325,8 +347,8 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
         const float py = fmaf(pr.R[3], dx, fmaf(pr.R[4], dy, pr.R[5] * dz));
         const float pz = fmaf(pr.R[6], dx, fmaf(pr.R[7], dy, pr.R[8] * dz));
         const float rho = sqrtf(fmaf(px, px, pz * pz));
-        const float th = atan2f(rho, py);
-        const float ph = atan2f(px, pz);
+        const float th = rot_atan2(rho, py);
+        const float ph = rot_atan2(px, pz);
         const float u = fmaf(th, a.u_scale, -0.5f);
         const float v = fmaf(ph, a.v_scale, -0.5f);
         const float fi = floorf(u), fj = floorf(v);
@@ -582,66 +604,111 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
       }
     }
   } else if (KIND == KIND_ROTATE) {
+    // row pairs: the two rows' 8 pixels per channel finish their two level-1
+    // blocks at once, so only one row pair of pixels is live at a time
     const ShiftParam pr = *p;
-    float x[CG][16];
+    float sp[4], cp[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int i = i0 + r;
-      const float st = __ldg(a.trig + i), ct = __ldg(a.trig + g.H + i);
-      int off[4][4];
-      float fu[4], fv[4];
+    for (int q = 0; q < 4; ++q) {
+      sp[q] = __ldg(a.trig + 2 * g.H + j0 + q);
+      cp[q] = __ldg(a.trig + 2 * g.H + g.W + j0 + q);
+    }
+    float A1[CG][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = j0 + q;
-        const float sp = __ldg(a.trig + 2 * g.H + j), cp = __ldg(a.trig + 2 * g.H + g.W + j);
-        const float dx = st * sp, dy = ct, dz = st * cp;
-        const float px = fmaf(pr.R[0], dx, fmaf(pr.R[1], dy, pr.R[2] * dz));
-        const float py = fmaf(pr.R[3], dx, fmaf(pr.R[4], dy, pr.R[5] * dz));
-        const float pz = fmaf(pr.R[6], dx, fmaf(pr.R[7], dy, pr.R[8] * dz));
-        const float rho = sqrtf(fmaf(px, px, pz * pz));
-        const float u = fmaf(atan2f(rho, py), a.u_scale, -0.5f);
-        const float v = fmaf(atan2f(px, pz), a.v_scale, -0.5f);
-        const float fi = floorf(u), fj = floorf(v);
-        fu[q] = u - fi;
-        fv[q] = v - fj;
-        const int ia = (int)fi, ja = (int)fj;
-        // taps: rows ia, ia+1 in [-1, H] (one step past a pole at most), columns cyclic
-        int r0 = ia, r1 = ia + 1, h0 = 0, h1 = 0;
-        if (g.boundary == HAAR_BOUNDARY_TORUS) {
-          r0 &= (g.H - 1);
-          r1 &= (g.H - 1);
-        } else {
-          if (r0 < 0) { r0 = -1 - r0; h0 = g.W >> 1; }
-          if (r0 >= g.H) { r0 = 2 * g.H - 1 - r0; h0 = g.W >> 1; }
-          if (r1 < 0) { r1 = -1 - r1; h1 = g.W >> 1; }
-          if (r1 >= g.H) { r1 = 2 * g.H - 1 - r1; h1 = g.W >> 1; }
+    for (int rp = 0; rp < 2; ++rp) {
+      float x[CG][8];
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int i = i0 + 2 * rp + rr;
+        const float st = __ldg(a.trig + i), ct = __ldg(a.trig + g.H + i);
+        int off[4][4];
+        float fu[4], fv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float dx = st * sp[q], dy = ct, dz = st * cp[q];
+          const float px = fmaf(pr.R[0], dx, fmaf(pr.R[1], dy, pr.R[2] * dz));
+          const float py = fmaf(pr.R[3], dx, fmaf(pr.R[4], dy, pr.R[5] * dz));
+          const float pz = fmaf(pr.R[6], dx, fmaf(pr.R[7], dy, pr.R[8] * dz));
+          const float rho = sqrtf(fmaf(px, px, pz * pz));
+          const float u = fmaf(rot_atan2(rho, py), a.u_scale, -0.5f);
+          const float v = fmaf(rot_atan2(px, pz), a.v_scale, -0.5f);
+          const float fi = floorf(u), fj = floorf(v);
+          fu[q] = u - fi;
+          fv[q] = v - fj;
+          const int ia = (int)fi, ja = (int)fj;
+          // taps: rows ia, ia+1 in [-1, H] (one step past a pole at most), columns cyclic
+          int r0 = ia, r1 = ia + 1, h0 = 0, h1 = 0;
+          if (g.boundary == HAAR_BOUNDARY_TORUS) {
+            r0 &= (g.H - 1);
+            r1 &= (g.H - 1);
+          } else {
+            if (r0 < 0) { r0 = -1 - r0; h0 = g.W >> 1; }
+            if (r0 >= g.H) { r0 = 2 * g.H - 1 - r0; h0 = g.W >> 1; }
+            if (r1 < 0) { r1 = -1 - r1; h1 = g.W >> 1; }
+            if (r1 >= g.H) { r1 = 2 * g.H - 1 - r1; h1 = g.W >> 1; }
+          }
+          off[q][0] = r0 * g.W + ((ja + h0) & Wm);
+          off[q][1] = r0 * g.W + ((ja + 1 + h0) & Wm);
+          off[q][2] = r1 * g.W + ((ja + h1) & Wm);
+          off[q][3] = r1 * g.W + ((ja + 1 + h1) & Wm);
         }
-        off[q][0] = r0 * g.W + ((ja + h0) & Wm);
-        off[q][1] = r0 * g.W + ((ja + 1 + h0) & Wm);
-        off[q][2] = r1 * g.W + ((ja + h1) & Wm);
-        off[q][3] = r1 * g.W + ((ja + 1 + h1) & Wm);
+#pragma unroll
+        for (int ci = 0; ci < CG; ++ci) {
+          if (ci < cgn) {
+            const float* F = a.pix + (long long)(c0 + ci) * g.N;
+            float f[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int t = 0; t < 4; ++t) f[q][t] = __ldg(F + off[q][t]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float w0 = (1.0f - fu[q]) * hsc, w1 = fu[q] * hsc;
+              x[ci][4 * rr + q] = w0 * ((1.0f - fv[q]) * f[q][0] + fv[q] * f[q][1]) +
+                                  w1 * ((1.0f - fv[q]) * f[q][2] + fv[q] * f[q][3]);
+            }
+          }
+        }
       }
+      // level 1 of the row pair's two 2 x 2 blocks (pixels pre-scaled by 1/2 on the fast path)
 #pragma unroll
       for (int ci = 0; ci < CG; ++ci) {
         if (ci < cgn) {
-          const float* F = a.pix + (long long)(c0 + ci) * g.N;
-          float f[4][4];
+          float D[3][2];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int sc = 0; sc < 2; ++sc) {
+            const float ea = x[ci][2 * sc], eb = x[ci][2 * sc + 1];
+            const float ec = x[ci][4 + 2 * sc], ed = x[ci][4 + 2 * sc + 1];
+            const float h = fast ? 1.0f : 0.5f;
+            A1[ci][2 * rp + sc] = h * ((ea + eb) + (ec + ed));
+            D[0][sc] = h * ((eb + ed) - (ea + ec));
+            D[1][sc] = h * ((ec + ed) - (ea + eb));
+            D[2][sc] = h * ((ea + ed) - (eb + ec));
+          }
+          const int r1 = ((tr * T) >> 1) + 2 * by + rp, c1 = ((tc * T) >> 1) + 2 * bx;
+          if (fast) {
+            float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)(c0 + ci) * a.st_c;
+            const int cols1 = g.W >> 1;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) f[q][t] = __ldg(F + off[q][t]);
+            for (int b = 0; b < 3; ++b)
+              *reinterpret_cast<float2*>(ob + g1 * (1 + b) + r1 * cols1 + c1) = make_float2(D[b][0], D[b][1]);
+          } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float w0 = (1.0f - fu[q]) * hsc, w1 = fu[q] * hsc;
-            x[ci][4 * r + q] = w0 * ((1.0f - fv[q]) * f[q][0] + fv[q] * f[q][1]) +
-                               w1 * ((1.0f - fv[q]) * f[q][2] + fv[q] * f[q][3]);
+            for (int sc = 0; sc < 2; ++sc) emit<OUT>(a, p, s, c0 + ci, 1, r1, c1 + sc, D[0][sc], D[1][sc], D[2][sc]);
           }
         }
       }
     }
+    // level 2 of the thread's block
 #pragma unroll
-    for (int ci = 0; ci < CG; ++ci)
-      if (ci < cgn) a2[ci] = levels12<OUT>(a, p, s, c0 + ci, x[ci], fast, tr, tc, by, bx);
+    for (int ci = 0; ci < CG; ++ci) {
+      if (ci < cgn) {
+        const float ea = A1[ci][0], eb = A1[ci][1], ec = A1[ci][2], ed = A1[ci][3];
+        emit<OUT>(a, p, s, c0 + ci, 2, ((tr * T) >> 2) + by, ((tc * T) >> 2) + bx, 0.5f * ((eb + ed) - (ea + ec)),
+                  0.5f * ((ec + ed) - (ea + eb)), 0.5f * ((ea + ed) - (eb + ec)));
+        a2[ci] = 0.5f * ((ea + eb) + (ec + ed));
+      }
+    }
   } else {  // KIND_COPY
     const float* F = a.pix + (long long)s * g.N;
     float x[16];
