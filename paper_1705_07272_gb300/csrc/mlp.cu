@@ -65,6 +65,16 @@ __device__ __forceinline__ float gelu(float z) {
   const float t = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
   return 0.5f * z * (1.0f + t);
 }
+// GELU of two values in one register pair (paired FP32 arithmetic; the two
+// tanh go through the SFU one by one)
+__device__ __forceinline__ unsigned long long gelu2(unsigned long long z) {
+  const unsigned long long u = f2_mul(z, z);
+  const unsigned long long t = f2_fma(u, f2_dup(kGeluA * kGeluB), f2_dup(kGeluA));   // A (1 + B z^2)
+  const float2 arg = u2f(f2_mul(t, z));                                                 // A (z + B z^3)
+  const unsigned long long th = f2_pack(tanh_fast(arg.x), tanh_fast(arg.y));
+  const unsigned long long hz = f2_mul(z, f2_dup(0.5f));
+  return f2_fma(hz, th, hz);                                                            // z (1 + tanh) / 2
+}
 __device__ __forceinline__ float gelu_grad(float z) {
   const float t = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * kGeluA * fmaf(3.0f * kGeluB, z * z, 1.0f);
@@ -279,29 +289,50 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
 // sin(w_f w) (3), cos(w_f w) (3) (columns 200..298); zeros to 320.
 constexpr int N_VCOLS = 200;
 
-__device__ __forceinline__ float omega(int f) { return 3.14159265358979323846f * exp2f(0.5f * (float)f); }
-
-__device__ __forceinline__ void encode_vertex_part(const float pn[6], __nv_bfloat16* out, int lane) {
-  for (int t = lane; t < N_FREQ * 6; t += 32) {
-    const int f = t / 6, r = t - f * 6;
-    float sv, cv;
-    sincosf(omega(f) * pn[r], &sv, &cv);
-    out[6 + 12 * f + r] = __float2bfloat16_rn(sv);
-    out[12 + 12 * f + r] = __float2bfloat16_rn(cv);
+// sin and cos of omega_f x for f = 0..15: omega_0 x = pi x and omega_1 x =
+// pi sqrt(2) x directly, the rest by the double-angle identities
+// (omega_{f+2} = 2 omega_f): sin 2a = 2 sin a cos a, cos 2a = (c - s)(c + s).
+// The doubled angles are exact (no FP32 rounding of a large argument); the
+// recurrence's error grows 2x per step, to ~1e-5 at f = 15, far below the
+// bfloat16 rounding of the stored features.
+__device__ __forceinline__ void sincos_ladder(float x, float (&sv)[N_FREQ], float (&cv)[N_FREQ]) {
+  sincosf(3.14159265358979323846f * x, &sv[0], &cv[0]);
+  sincosf(4.44288293815836624702f * x, &sv[1], &cv[1]);
+#pragma unroll
+  for (int f = 2; f < N_FREQ; ++f) {
+    const float sa = sv[f - 2], ca = cv[f - 2];
+    sv[f] = 2.0f * sa * ca;
+    cv[f] = (ca - sa) * (ca + sa);
   }
-  if (lane < 6) out[lane] = __float2bfloat16_rn(pn[lane]);
+}
+
+// lane r < 6 encodes component r of [p, n]
+__device__ __forceinline__ void encode_vertex_part(const float pn[6], __nv_bfloat16* out, int lane) {
+  if (lane < 6) {
+    float sv[N_FREQ], cv[N_FREQ];
+    sincos_ladder(pn[lane], sv, cv);
+#pragma unroll
+    for (int f = 0; f < N_FREQ; ++f) {
+      out[6 + 12 * f + lane] = __float2bfloat16_rn(sv[f]);
+      out[12 + 12 * f + lane] = __float2bfloat16_rn(cv[f]);
+    }
+    out[lane] = __float2bfloat16_rn(pn[lane]);
+  }
   if (lane < 2) out[198 + lane] = __float2bfloat16_rn(0.0f);
 }
 
+// lane r < 3 encodes component r of the view direction w
 __device__ __forceinline__ void encode_view_part(const float w[3], __nv_bfloat16* out, int lane) {
-  for (int t = lane; t < N_FREQ * 3; t += 32) {
-    const int f = t / 3, r = t - f * 3;
-    float sv, cv;
-    sincosf(omega(f) * w[r], &sv, &cv);
-    out[203 + 6 * f + r] = __float2bfloat16_rn(sv);
-    out[206 + 6 * f + r] = __float2bfloat16_rn(cv);
+  if (lane < 3) {
+    float sv[N_FREQ], cv[N_FREQ];
+    sincos_ladder(w[lane], sv, cv);
+#pragma unroll
+    for (int f = 0; f < N_FREQ; ++f) {
+      out[203 + 6 * f + lane] = __float2bfloat16_rn(sv[f]);
+      out[206 + 6 * f + lane] = __float2bfloat16_rn(cv[f]);
+    }
+    out[200 + lane] = __float2bfloat16_rn(w[lane]);
   }
-  if (lane < 3) out[200 + lane] = __float2bfloat16_rn(w[lane]);
   for (int j = 299 + lane; j < N_IN; j += 32) out[j] = __float2bfloat16_rn(0.0f);
 }
 
@@ -540,6 +571,11 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
   __shared__ FBars bars;
   __shared__ int rinfo[8][16][2];
   __shared__ float rview[8][16][3];
+  __shared__ __align__(16) float sbias[3][WIDTH];        // hidden-layer biases 1..3 (the last one folds into beff)
+  __shared__ __align__(16) float sbias3[WIDTH];          // bias of the 4th hidden layer
+  // per epilogue warp: its column half of the folded output layer for the
+  // tile's (at most two) shifts, so that no barrier across warps is needed
+  __shared__ __align__(16) float sweff[8][2][WIDTH / 2][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* act = smem_raw + (base - smem_u32(smem_raw));
@@ -563,6 +599,11 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&bars.tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int i = threadIdx.x; i < 4 * WIDTH; i += blockDim.x) {
+    const int l = i / WIDTH, j = i - l * WIDTH;
+    const float bv = f.params[b_off(l) + j];
+    if (l < 3) sbias[l][j] = bv; else sbias3[j] = bv;
   }
   fence_before();
   __syncthreads();
@@ -638,6 +679,25 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
     bool ok = true;
     for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const long long row0 = t * BM;
+      // ---- this warp's column half of the tile's folded output layer (the
+      // tile's rows span at most two shifts)
+      const int s_lo = (int)(row0 / f.V);
+      const int s_hi = (int)((row0 + BM - 1 < f.rows ? row0 + BM - 1 : f.rows - 1) / f.V);
+      {
+        const int hw = (wid >> 2) * (WIDTH / 2);
+        __syncwarp();
+        for (int i = lane; i < WIDTH; i += 32) {
+          const int k = i / (WIDTH / 2), j = i - k * (WIDTH / 2);
+          const float* W = f.weff + ((long long)(k ? s_hi : s_lo) * WIDTH + hw + j) * f.C;
+          float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          w4.x = W[0];
+          if (f.C > 1) w4.y = W[1];
+          if (f.C > 2) w4.z = W[2];
+          if (f.C > 3) w4.w = W[3];
+          *reinterpret_cast<float4*>(&sweff[wid][k][j][0]) = w4;
+        }
+        __syncwarp();
+      }
       // ---- encode 16 rows per warp: row info first, then many independent
       // loads / sincos per lane (lanes sweep (row, chunk) pairs)
       const int r0 = wid * 16;
@@ -669,14 +729,19 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
         if (sr >= 0) val = __ldg(reinterpret_cast<const uint4*>(f.vfeat + (long long)rinfo[wid][i][1] * N_VCOLS) + ch);
         *reinterpret_cast<uint4*>(act + act_off(r0 + i, 8 * ch)) = val;
       }
-#pragma unroll 4
-      for (int e = lane; e < 16 * N_FREQ * 3; e += 32) {
-        const int i = e / (N_FREQ * 3), t2 = e - i * (N_FREQ * 3);
-        const int fq = t2 / 3, rr = t2 - fq * 3;
-        float sv = 0.0f, cv = 0.0f;
-        if (rinfo[wid][i][0] >= 0) sincosf(omega(fq) * rview[wid][i][rr], &sv, &cv);
-        *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, 203 + 6 * fq + rr)) = __float2bfloat16_rn(sv);
-        *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, 206 + 6 * fq + rr)) = __float2bfloat16_rn(cv);
+      // view features: one lane per (row, component), all 16 frequencies by the ladder
+      for (int e = lane; e < 16 * 3; e += 32) {
+        const int i = e / 3, rr = e - i * 3;
+        float sv[N_FREQ], cv[N_FREQ];
+        sincos_ladder(rview[wid][i][rr], sv, cv);
+        const bool live = rinfo[wid][i][0] >= 0;
+#pragma unroll
+        for (int fq = 0; fq < N_FREQ; ++fq) {
+          *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, 203 + 6 * fq + rr)) =
+              __float2bfloat16_rn(live ? sv[fq] : 0.0f);
+          *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, 206 + 6 * fq + rr)) =
+              __float2bfloat16_rn(live ? cv[fq] : 0.0f);
+        }
       }
       for (int e = lane; e < 16 * 24; e += 32) {       // raw view (3) and the zero pad (21)
         const int i = e / 24, j = e - i * 24;
@@ -694,11 +759,11 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       for (int l = 0; l < 4; ++l, ++step) {
         if (!mbar_wait(smem_u32(&bars.tfull), (uint32_t)(step & 1), status, abort_flag)) { ok = false; break; }
         fence_after();
-        const float* bias = f.params + b_off(l);
+        const float* bias = (l < 3) ? sbias[l] : sbias3;
         float acc_c[4] = {0.f, 0.f, 0.f, 0.f};
         int s = 0;
         if (l == 3 && row_ok) s = (int)(row / f.V);
-        const float* W = f.weff + (long long)s * WIDTH * f.C;
+        const float(*Wt)[4] = sweff[wid][(l == 3 && s != s_lo) ? 1 : 0];   // column c0 + i at [c0 + i - 128 half]
         for (int cc = 0; cc < 4; ++cc) {
           const int c0 = half * 128 + cc * 32;
           float v[32];
@@ -707,8 +772,9 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
             uint32_t pk[16];
 #pragma unroll
             for (int i = 0; i < 32; i += 2) {
-              __nv_bfloat162 hb = __floats2bfloat162_rn(gelu(v[i] + __ldg(bias + c0 + i)),
-                                                        gelu(v[i + 1] + __ldg(bias + c0 + i + 1)));
+              const float2 b2 = *reinterpret_cast<const float2*>(bias + c0 + i);
+              const float2 h = u2f(gelu2(f2_add(f2_pack(v[i], v[i + 1]), f2_pack(b2.x, b2.y))));
+              __nv_bfloat162 hb = __floats2bfloat162_rn(h.x, h.y);
               pk[i >> 1] = *reinterpret_cast<uint32_t*>(&hb);
             }
 #pragma unroll
@@ -717,11 +783,15 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
                   make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
           } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float h = gelu(v[i] + __ldg(bias + c0 + i));
-#pragma unroll
-              for (int c = 0; c < 4; ++c)
-                if (c < f.C) acc_c[c] = fmaf(h, __ldg(W + (long long)(c0 + i) * f.C + c), acc_c[c]);
+            for (int i = 0; i < 32; i += 2) {
+              const float2 b2 = *reinterpret_cast<const float2*>(bias + c0 + i);
+              const float2 h = u2f(gelu2(f2_add(f2_pack(v[i], v[i + 1]), f2_pack(b2.x, b2.y))));
+              const float4 wa = *reinterpret_cast<const float4*>(Wt[c0 - half * 128 + i]);
+              const float4 wb = *reinterpret_cast<const float4*>(Wt[c0 - half * 128 + i + 1]);
+              acc_c[0] = fmaf(h.y, wb.x, fmaf(h.x, wa.x, acc_c[0]));
+              acc_c[1] = fmaf(h.y, wb.y, fmaf(h.x, wa.y, acc_c[1]));
+              acc_c[2] = fmaf(h.y, wb.z, fmaf(h.x, wa.z, acc_c[2]));
+              acc_c[3] = fmaf(h.y, wb.w, fmaf(h.x, wa.w, acc_c[3]));
             }
           }
         }

@@ -176,28 +176,6 @@ __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restri
 constexpr int kGroup = HAAR_GCSR_GROUP;
 static_assert(kGroup == 4, "lane layout below assumes 4-vertex groups");
 
-// Paired FP32 arithmetic of sm_100+ (fma.rn.f32x2): two lanes of a 64-bit
-// register pair per instruction, each rounded like fmaf.
-__device__ __forceinline__ unsigned long long f2_dup(float a) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2_shfl_xor(unsigned long long a, int o) {
-  return __shfl_xor_sync(0xffffffffu, a, o);
-}
-
 // Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
 __device__ __forceinline__ void l2_prefetch_bulk(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
