@@ -518,19 +518,25 @@ __global__ void __launch_bounds__(256) k_fold(const float* __restrict__ p, const
 }
 
 // ----------------------------------------------------------- fused surrogate shading
-// Persistent, one CTA per SM, 10 warps, one 128-row tile at a time (rows are
+// Persistent, one CTA per SM, 18 warps, one 128-row tile at a time (rows are
 // (shift, vertex) pairs, row = s * V + v):
 //   warp 0     TMA producer: the weight k-blocks [256 x 64] of W1..W4 into a
 //              3-stage ring, in the order the MMAs use them, tile after tile;
 //   warp 1     TMEM allocator and MMA issuer (M = 128, N = 256, K = 16);
-//   warps 2-9  encode the tile into the activation buffer (the 200
+//   warps 2-17 encode the tile into the activation buffer (the 200
 //              per-vertex columns copied from a table, the view columns
 //              computed), then each layer's epilogue: bias + GELU, written
 //              back as the next layer's bf16 A operand in the same
 //              128-byte-swizzled K-major layout the tensor core reads; the
 //              last layer's epilogue takes the double product with the output
-//              layer folded into the lighting.  Activations never leave the SM.
-constexpr int F_THREADS = 320;
+//              layer folded into the lighting; the 4 column groups of a TMEM
+//              lane quarter meet in shared memory (an mbarrier per quarter) and
+//              group 0 adds them in a fixed order and writes the radiance.
+//              Activations never leave the SM.
+constexpr int F_EPI = 16;                    // epilogue warps: 4 per TMEM lane quarter
+constexpr int F_RPW = tc::BM / F_EPI;        // rows each epilogue warp encodes
+constexpr int F_COLS = WIDTH / (F_EPI / 4);  // columns each epilogue warp takes per layer
+constexpr int F_THREADS = 64 + 32 * F_EPI;
 constexpr int F_STAGES = 3;
 constexpr uint32_t F_ACT_BYTES = 5 * 16384;  // 128 rows x 320 bf16
 constexpr uint32_t F_W_BYTES = 256 * 128;    // one weight k-block [256 x 64] bf16
@@ -538,6 +544,7 @@ constexpr uint32_t F_W_BYTES = 256 * 128;    // one weight k-block [256 x 64] bf
 struct __align__(8) FBars {
   uint64_t wfull[F_STAGES], wempty[F_STAGES];
   uint64_t tfull, aready, drain;
+  uint64_t red[4];                 // per lane quarter: the 4 column groups' partial radiance are in
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -551,7 +558,7 @@ struct FusedArgs {
   const float* params;         // flat parameters (biases)
   const float* weff;           // [S][256][C]
   const float* beff;           // [S][C]
-  float* radiance;             // [V][S][C], zeroed before the launch
+  float* radiance;             // [V][S][C]
 };
 
 // byte offset of element (r, c) in the activation buffer: k-block c/64 is a
@@ -569,13 +576,15 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
   using namespace tc;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ FBars bars;
-  __shared__ int rinfo[8][16][2];
-  __shared__ float rview[8][16][3];
+  __shared__ int rinfo[F_EPI][F_RPW][2];
+  __shared__ float rview[F_EPI][F_RPW][3];
   __shared__ __align__(16) float sbias[3][WIDTH];        // hidden-layer biases 1..3 (the last one folds into beff)
   __shared__ __align__(16) float sbias3[WIDTH];          // bias of the 4th hidden layer
-  // per epilogue warp: its column half of the folded output layer for the
+  // per epilogue warp: its column group of the folded output layer for the
   // tile's (at most two) shifts, so that no barrier across warps is needed
-  __shared__ __align__(16) float sweff[8][2][WIDTH / 2][4];
+  __shared__ __align__(16) float sweff[F_EPI][2][F_COLS][4];
+  // per lane quarter: the partial radiance of column groups 1..3 for group 0
+  __shared__ __align__(16) float sred[4][3][32][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* act = smem_raw + (base - smem_u32(smem_raw));
@@ -590,7 +599,8 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       mbar_init(smem_u32(&bars.wempty[i]), 1);
     }
     mbar_init(smem_u32(&bars.tfull), 1);
-    mbar_init(smem_u32(&bars.aready), 8);
+    mbar_init(smem_u32(&bars.aready), F_EPI);
+    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars.red[i]), 3);
     mbar_init(smem_u32(&bars.drain), 1);
     bars.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -672,23 +682,23 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       }
     }
   } else {
-    const int wid = warp - 2;                 // 0..7
+    const int wid = warp - 2;                 // 0..F_EPI-1
     const int q = warp & 3;                   // TMEM lane quarter
-    const int half = wid >> 2;                // column half
+    const int cg = wid >> 2;                  // column group: columns [cg F_COLS, (cg + 1) F_COLS)
     long long step = 0;
+    long long it = 0;                         // tiles done (phase of the reduction barrier)
     bool ok = true;
-    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++it) {
       const long long row0 = t * BM;
-      // ---- this warp's column half of the tile's folded output layer (the
+      // ---- this warp's column group of the tile's folded output layer (the
       // tile's rows span at most two shifts)
       const int s_lo = (int)(row0 / f.V);
       const int s_hi = (int)((row0 + BM - 1 < f.rows ? row0 + BM - 1 : f.rows - 1) / f.V);
       {
-        const int hw = (wid >> 2) * (WIDTH / 2);
         __syncwarp();
-        for (int i = lane; i < WIDTH; i += 32) {
-          const int k = i / (WIDTH / 2), j = i - k * (WIDTH / 2);
-          const float* W = f.weff + ((long long)(k ? s_hi : s_lo) * WIDTH + hw + j) * f.C;
+        for (int i = lane; i < 2 * F_COLS; i += 32) {
+          const int k = i / F_COLS, j = i - k * F_COLS;
+          const float* W = f.weff + ((long long)(k ? s_hi : s_lo) * WIDTH + cg * F_COLS + j) * f.C;
           float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
           w4.x = W[0];
           if (f.C > 1) w4.y = W[1];
@@ -698,10 +708,10 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
         }
         __syncwarp();
       }
-      // ---- encode 16 rows per warp: row info first, then many independent
-      // loads / sincos per lane (lanes sweep (row, chunk) pairs)
-      const int r0 = wid * 16;
-      if (lane < 16) {
+      // ---- encode F_RPW rows per warp: row info first, then many independent
+      // loads per lane (lanes sweep (row, chunk) pairs)
+      const int r0 = wid * F_RPW;
+      if (lane < F_RPW) {
         const long long row = row0 + r0 + lane;
         int sr = -1, vr = 0;
         float w0 = 0.f, w1 = 0.f, w2 = 0.f;
@@ -722,7 +732,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       }
       __syncwarp();
 #pragma unroll 4
-      for (int e = lane; e < 16 * 25; e += 32) {
+      for (int e = lane; e < F_RPW * 25; e += 32) {
         const int i = e / 25, ch = e - i * 25;
         const int sr = rinfo[wid][i][0];
         uint4 val = make_uint4(0, 0, 0, 0);
@@ -730,8 +740,8 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
         *reinterpret_cast<uint4*>(act + act_off(r0 + i, 8 * ch)) = val;
       }
       // view features: one lane per (row, component), all 16 frequencies by the ladder
-      for (int e = lane; e < 16 * 3; e += 32) {
-        const int i = e / 3, rr = e - i * 3;
+      if (lane < F_RPW * 3) {
+        const int i = lane / 3, rr = lane - i * 3;
         float sv[N_FREQ], cv[N_FREQ];
         sincos_ladder(rview[wid][i][rr], sv, cv);
         const bool live = rinfo[wid][i][0] >= 0;
@@ -743,7 +753,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
               __float2bfloat16_rn(live ? cv[fq] : 0.0f);
         }
       }
-      for (int e = lane; e < 16 * 24; e += 32) {       // raw view (3) and the zero pad (21)
+      for (int e = lane; e < F_RPW * 24; e += 32) {    // raw view (3) and the zero pad (21)
         const int i = e / 24, j = e - i * 24;
         const float x = (j < 3 && rinfo[wid][i][0] >= 0) ? rview[wid][i][j] : 0.0f;
         *reinterpret_cast<__nv_bfloat16*>(act + act_off(r0 + i, (j < 3) ? 200 + j : 296 + j)) = __float2bfloat16_rn(x);
@@ -763,9 +773,9 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
         float acc_c[4] = {0.f, 0.f, 0.f, 0.f};
         int s = 0;
         if (l == 3 && row_ok) s = (int)(row / f.V);
-        const float(*Wt)[4] = sweff[wid][(l == 3 && s != s_lo) ? 1 : 0];   // column c0 + i at [c0 + i - 128 half]
-        for (int cc = 0; cc < 4; ++cc) {
-          const int c0 = half * 128 + cc * 32;
+        const float(*Wt)[4] = sweff[wid][(l == 3 && s != s_lo) ? 1 : 0];   // column c0 + i at [c0 + i - cg F_COLS]
+        for (int cc = 0; cc < F_COLS / 32; ++cc) {
+          const int c0 = cg * F_COLS + cc * 32;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
           if (l < 3) {
@@ -786,8 +796,8 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
             for (int i = 0; i < 32; i += 2) {
               const float2 b2 = *reinterpret_cast<const float2*>(bias + c0 + i);
               const float2 h = u2f(gelu2(f2_add(f2_pack(v[i], v[i + 1]), f2_pack(b2.x, b2.y))));
-              const float4 wa = *reinterpret_cast<const float4*>(Wt[c0 - half * 128 + i]);
-              const float4 wb = *reinterpret_cast<const float4*>(Wt[c0 - half * 128 + i + 1]);
+              const float4 wa = *reinterpret_cast<const float4*>(Wt[c0 - cg * F_COLS + i]);
+              const float4 wb = *reinterpret_cast<const float4*>(Wt[c0 - cg * F_COLS + i + 1]);
               acc_c[0] = fmaf(h.y, wb.x, fmaf(h.x, wa.x, acc_c[0]));
               acc_c[1] = fmaf(h.y, wb.y, fmaf(h.x, wa.y, acc_c[1]));
               acc_c[2] = fmaf(h.y, wb.z, fmaf(h.x, wa.z, acc_c[2]));
@@ -800,13 +810,25 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&bars.aready));
-        } else if (row_ok) {
-          // the two column halves add into the zeroed output (two adds onto
-          // zero commute exactly, so the result does not depend on their order)
-          const int vv = (int)(row - (long long)s * f.V);
-          for (int c = 0; c < f.C; ++c)
-            atomicAdd(f.radiance + ((long long)vv * f.S + s) * f.C + c,
-                      acc_c[c] + (half == 0 ? f.beff[s * f.C + c] : 0.0f));
+        } else {
+          // the 4 column groups of this lane quarter meet in group 0, which adds
+          // them in a fixed order (deterministic) and writes the radiance
+          if (cg > 0) {
+            *reinterpret_cast<float4*>(&sred[q][cg - 1][lane][0]) = make_float4(acc_c[0], acc_c[1], acc_c[2], acc_c[3]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars.red[q]));
+          } else {
+            if (!mbar_wait(smem_u32(&bars.red[q]), (uint32_t)(it & 1), status, abort_flag)) { ok = false; break; }
+            if (row_ok) {
+              const int vv = (int)(row - (long long)s * f.V);
+              for (int c = 0; c < f.C; ++c) {
+                float tsum = acc_c[c];
+#pragma unroll
+                for (int g2 = 0; g2 < 3; ++g2) tsum += sred[q][g2][lane][c];
+                f.radiance[((long long)vv * f.S + s) * f.C + c] = tsum + f.beff[s * f.C + c];
+              }
+            }
+          }
         }
       }
     }
@@ -1215,7 +1237,6 @@ haar_status_t haar_mlp_shade(haar_mlp_t M, int V, int S, const float* pos, const
     // fused: per-vertex features once, then every layer on chip
     k_vertex_features<<<(V + 7) / 8, 256, 0, st>>>(pos, nrm, V, M->iX);
     HS_TRY(cuda_check(cudaGetLastError(), "k_vertex_features launch"));
-    HS_TRY(cuda_check(cudaMemsetAsync(radiance, 0, sizeof(float) * (size_t)rows * C, st), "haar_mlp_shade: zero radiance"));
     CUtensorMap wm[4];
     for (int l = 0; l < 4; ++l)
       if (!encode_2d(&wm[l], M->wb + wb_off(l), (uint64_t)fan_in(l), (uint64_t)WIDTH, tc::BK, WIDTH))
