@@ -316,3 +316,22 @@ def test_start_level_rotation_matches_oracle(hs):
     ref = osh.haar_shift(c, H, W, osh.ROTATE_EULER, eul, start_level=1)
     assert got.shape == ref.shape == (8, 3, (H * W) >> 2)
     assert rel_l2(got, ref, axis=(1, 2)).max() <= ROT_TOL
+
+
+def test_whole_map_kernel_layouts_and_truncation(hs):
+    # enough (channel, shift) items for the whole-map kernel (map held in shared
+    # memory): every layout and a truncated K give the bits of the full SCK result
+    H, W = 128, 256
+    c = _lighting(3, H, W, 77)
+    rng = np.random.default_rng(77)
+    prm = np.stack([rng.uniform(-W, W, 110), rng.uniform(-2 * H, 2 * H, 110)], axis=1)
+    prm[3] = [128.0, 64.0]                                    # dyadic: permuted levels
+    base, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_SCK)
+    sample = [0, 3, 57, 109]
+    ref = osh.haar_shift(c, H, W, osh.TRANSLATE, prm[sample])
+    assert rel_l2(base[sample], ref, axis=(1, 2)).max() <= 1e-5
+    for lay in (hs.HAAR_LAYOUT_SKC, hs.HAAR_LAYOUT_KSC):
+        o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, lay)
+        assert np.array_equal(o, base)
+    o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_SKC, K=1000)
+    assert np.array_equal(o, base[..., :1000])
