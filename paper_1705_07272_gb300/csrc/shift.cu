@@ -526,6 +526,26 @@ __device__ __forceinline__ float levels12(const ShiftArgs& a, const ShiftParam* 
 __device__ __forceinline__ void named_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
+// merge4 for the fast path (float32, k contiguous, no permuted level): the
+// stores go to the (shift, channel) plane `ob` directly.
+__device__ __forceinline__ float merge4f(float* ob, const Geometry& g, int K, float A, int lane, int st, int sh,
+                                         int lvl, int i0, int j0, int by, int bx, int limit = 32) {
+  const int base = lane & ~(4 * st - 1);
+  const float e0 = __shfl_sync(0xffffffffu, A, base);
+  const float e1 = __shfl_sync(0xffffffffu, A, base + st);
+  const float e2 = __shfl_sync(0xffffffffu, A, base + 2 * st);
+  const float e3 = __shfl_sync(0xffffffffu, A, base + 3 * st);
+  const int m = (lane - base) >> sh;
+  if ((lane & (st - 1)) == 0 && m < 3 && lane < limit) {
+    const float d = (m == 0) ? 0.5f * ((e1 + e3) - (e0 + e2))
+                  : (m == 1) ? 0.5f * ((e2 + e3) - (e0 + e1)) : 0.5f * ((e0 + e3) - (e1 + e2));
+    const int gl = g.q << (2 * (g.n - lvl));
+    const int k = gl * (1 + m) + ((i0 >> lvl) + (by >> (lvl - 2))) * (g.W >> lvl) + (j0 >> lvl) + (bx >> (lvl - 2));
+    if (k < K) ob[k] = d;
+  }
+  return 0.5f * ((e0 + e1) + (e2 + e3));
+}
+
 // Register path for 32 x 32 and 64 x 64 tiles: every thread resamples its own
 // 4 x 4 block of output pixels for up to CG channels straight from
 // the L2-resident pixel map (translation: a 5 x 8 aligned window of float4
@@ -724,32 +744,46 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
   // one value per 16 lanes remains and goes to shared memory
   const int lane = threadIdx.x & 31;
   const int nthreads = nb * nb;
+  const int nwarps = nthreads >> 5;
   const int groups = nthreads >> 4;
   float* sA = smem;                                 // [CG][groups]
 #pragma unroll
   for (int ci = 0; ci < CG; ++ci) {
     if (ci < cgn) {
-      float A = merge4<OUT>(a, p, s, c0 + ci, a2[ci], lane, 1, 0, 3, tr * T, tc * T, by, bx);
-      A = merge4<OUT>(a, p, s, c0 + ci, A, lane, 4, 2, 4, tr * T, tc * T, by, bx);
+      float A;
+      if (fast) {
+        float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)(c0 + ci) * a.st_c;
+        A = merge4f(ob, g, a.K, a2[ci], lane, 1, 0, 3, tr * T, tc * T, by, bx);
+        A = merge4f(ob, g, a.K, A, lane, 4, 2, 4, tr * T, tc * T, by, bx);
+      } else {
+        A = merge4<OUT>(a, p, s, c0 + ci, a2[ci], lane, 1, 0, 3, tr * T, tc * T, by, bx);
+        A = merge4<OUT>(a, p, s, c0 + ci, A, lane, 4, 2, 4, tr * T, tc * T, by, bx);
+      }
       if ((lane & 15) == 0) sA[ci * groups + (threadIdx.x >> 4)] = A;
     }
   }
-  if (threadIdx.x >= 32) {
+  // warps that finish a channel's tile below stay; the others leave
+  const int wid = threadIdx.x >> 5;
+  if (wid >= cgn) {
     named_arrive(1, nthreads);
     return;
   }
   named_sync(1, nthreads);
   pdl_trigger();                                  // the tile's levels 1-4 are written
 
-  // warp 0: levels 5..Lt on the `groups` values of each channel (a Morton-
-  // ordered grid of 16 x 16-pixel blocks)
+  // warp w: levels 5..Lt of channels w, w + nwarps, ... on the `groups`
+  // values (a Morton-ordered grid of 16 x 16-pixel blocks), then the tile
+  // mean; the last arrival of a shift runs its coarse levels
   const int gy = morton_y(lane) << 2, gx = morton_x(lane) << 2;
-  for (int ci = 0; ci < cgn; ++ci) {
+  unsigned last = 0;
+  for (int ci = wid; ci < cgn; ci += nwarps) {
     const int c = c0 + ci;
     float B = (lane < groups) ? sA[ci * groups + lane] : 0.0f;
     int st2 = 1, sh2 = 0;
+    float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)c * a.st_c;
     for (int lvl = 4; lvl < g.Lt; ++lvl) {
-      B = merge4<OUT>(a, p, s, c, B, lane, st2, sh2, lvl + 1, tr * T, tc * T, gy, gx, groups);
+      B = fast ? merge4f(ob, g, a.K, B, lane, st2, sh2, lvl + 1, tr * T, tc * T, gy, gx, groups)
+               : merge4<OUT>(a, p, s, c, B, lane, st2, sh2, lvl + 1, tr * T, tc * T, gy, gx, groups);
       st2 *= 4;
       sh2 += 2;
     }
@@ -759,19 +793,19 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
       else
         reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = B;
     }
+    if (a.counters != nullptr && lane == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(a.counters + s, 1u);
+      if (t == (unsigned)(g.n_tiles * g.C - 1)) last = 1u;
+    }
   }
   if (a.counters == nullptr) return;
-  unsigned last = 0;
-  if (lane == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(a.counters + s, 1u);
-    last = (t == (unsigned)(g.n_tiles * gridDim.z - 1)) ? 1u : 0u;
-  }
   last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return;
   __threadfence();
-  float* img = smem;
-  float* img2 = smem + ((g.n_tiles + 3) & ~3);   // float4-aligned
+  // past sA, which the CTA's other warps may still be reading
+  float* img = smem + ((CG * groups + 3) & ~3);
+  float* img2 = img + ((g.n_tiles + 3) & ~3);   // float4-aligned
   for (int c = 0; c < g.C; ++c) {
     for (int t = lane; t < g.n_tiles; t += 32)
       img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
@@ -1103,9 +1137,11 @@ static size_t shift_smem_bytes(const Geometry& g, int kind) {
 template <int KIND, int OUT, int CG>
 static haar_status_t launch_reg(const ShiftArgs& a, int S, cudaStream_t st) {
   const int nb = a.g.T / 4;
-  size_t fl = (size_t)CG * nb * nb + (size_t)(nb / 4) * (nb / 4) + 8;
-  const size_t coarse = (size_t)a.g.n_tiles + (size_t)a.g.n_tiles / 4 + 8;
-  if (fl < coarse) fl = coarse;
+  // shared floats: the group values sA [CG][nb^2 / 16], then (last CTA of a
+  // shift) the tile-mean image and its scratch, each float4-aligned
+  const size_t sa = ((size_t)CG * nb * nb / 16 + 3) & ~(size_t)3;
+  const size_t nt4 = ((size_t)a.g.n_tiles + 3) & ~(size_t)3;
+  const size_t fl = sa + nt4 + (size_t)a.g.n_tiles / 4 + 16;
   const size_t sm = fl * sizeof(float);
   auto fr = k_shift_reg<KIND, OUT, CG>;
   if (sm > 48 * 1024) {
