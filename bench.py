@@ -347,7 +347,7 @@ def measure_rows(hs, dev, flush, only=None):
         plan.close()
         del T, lit, R, tr
 
-    # c3 frame: view bins + 32 rotations (FP32 SKC) + view-binned top-512 FP16 shading
+    # c3 frame: view bins + 32 rotations (FP32 SKC4) + view-binned top-512 FP16 shading
     c3 = None
     if want("c3_bincsr") or want("c4_surrogate") or want("surrogate_training"):
         sc3 = synth.scene(3)
@@ -357,7 +357,7 @@ def measure_rows(hs, dev, flush, only=None):
         pos, nrm, cams, dirs = f(sc3["pos"]), f(sc3["nrm"]), f(sc3["cams"]), f(synth.view_bin_dirs(16))
         eul3 = torch.tensor(sc3["params"], dtype=torch.float64, device=dev)
         L3 = hs.haar_forward(torch.tensor(sc3["light"], dtype=torch.float32, device=dev))
-        plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_layout=hs.HAAR_LAYOUT_SKC)
+        plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_layout=hs.HAAR_LAYOUT_SKC4)
         lit = torch.empty(plan.out_shape(S), dtype=torch.float32, device=dev)
         bins = torch.empty((S, V), dtype=torch.uint8, device=dev)
         R = torch.empty((V, S, 3), dtype=torch.float32, device=dev)
@@ -396,7 +396,7 @@ def measure_rows(hs, dev, flush, only=None):
         net.set_params(torch.tensor(np.concatenate(flat), dtype=torch.float32, device=dev))
         R4 = torch.empty((V, S, 3), dtype=torch.float32, device=dev)
         N3 = 131072
-        strides = (N3 * 3, 1, 3)
+        strides = (N3 * 4, 1, 4)                    # SKC4 lighting
         if want("c4_surrogate"):
             def c4_frame():
                 hs.haar_shift(plan, L3, eul3, lit)

@@ -86,7 +86,10 @@ typedef enum {
 typedef enum {
   HAAR_LAYOUT_SCK = 0, /* out[s][c][k] */
   HAAR_LAYOUT_SKC = 1, /* out[s][k][c]  (channels interleaved) */
-  HAAR_LAYOUT_KSC = 2  /* out[k][s][c]  (coefficient-major) */
+  HAAR_LAYOUT_KSC = 2, /* out[k][s][c]  (coefficient-major) */
+  HAAR_LAYOUT_SKC4 = 3 /* out[s][k][4]: SKC with the channel axis padded to 4 (C <= 4; the
+                          pad entries are not written), so a coefficient's channels are one
+                          16-byte vector for gathers */
 } haar_layout_t;
 
 typedef struct haar_shift_plan_s* haar_shift_plan_t;
@@ -212,7 +215,7 @@ typedef struct {
  *                    K % 64 == 0 (tcgen05 tensor-core GEMM, FP32 accumulate,
  *                    T x L_hi + T x L_lo);
  *   CSR_F32_U16      with F32  lighting, layout KSC (S*C % 4 == 0);
- *   BINCSR_F16_U32   with F32  lighting, layout SKC;
+ *   BINCSR_F16_U32   with F32  lighting, layout SKC or SKC4;
  *   GCSR_F32_U16     with F32  lighting, layout KSC (S*C % 4 == 0).
  * radiance: [V][S][C] float32, overwritten.  Launches that use the same plan
  * must be ordered (one stream, or events): the plan's workspace and device

@@ -38,6 +38,7 @@ HAAR_OUT_F16 = 2
 HAAR_LAYOUT_SCK = 0
 HAAR_LAYOUT_SKC = 1
 HAAR_LAYOUT_KSC = 2
+HAAR_LAYOUT_SKC4 = 3
 # haar_transport_kind_t
 HAAR_T_DENSE_F32 = 0
 HAAR_T_DENSE_BF16 = 1
@@ -199,6 +200,8 @@ class Plan:
         planes = 2 if self.out_type == HAAR_OUT_BF16_HILO else 1
         if self.out_layout == HAAR_LAYOUT_SCK:
             shp = (S, self.C, self.K)
+        elif self.out_layout == HAAR_LAYOUT_SKC4:
+            shp = (S, self.K, 4)
         elif self.out_layout == HAAR_LAYOUT_SKC:
             shp = (S, self.K, self.C)
         else:

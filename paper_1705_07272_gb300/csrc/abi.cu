@@ -98,8 +98,10 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: out_coeffs %d not in [0, %lld]", d->out_coeffs, N);
   if (d->out_type < HAAR_OUT_F32 || d->out_type > HAAR_OUT_F16)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: unknown out_type %d", d->out_type);
-  if (d->out_layout < HAAR_LAYOUT_SCK || d->out_layout > HAAR_LAYOUT_KSC)
+  if (d->out_layout < HAAR_LAYOUT_SCK || d->out_layout > HAAR_LAYOUT_SKC4)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: unknown out_layout %d", d->out_layout);
+  if (d->out_layout == HAAR_LAYOUT_SKC4 && d->channels > 4)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: SKC4 holds at most 4 channels (got %d)", d->channels);
 
   haar_shift_plan_s* p = new (std::nothrow) haar_shift_plan_s();
   if (!p) return set_error(HAAR_ERR_NOMEM, "haar_shift_plan: host allocation failed");
@@ -112,7 +114,7 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
   cudaGetDevice(&p->device);
   const Geometry& g = p->geo;
   const size_t S = d->max_shifts;
-  p->light_elems = S * g.C * (size_t)p->K;
+  p->light_elems = S * (d->out_layout == HAAR_LAYOUT_SKC4 ? 4 : g.C) * (size_t)p->K;
   const size_t light_bytes =
       p->light_elems * out_elem_bytes(d->out_type) * (d->out_type == HAAR_OUT_BF16_HILO ? 2 : 1);
   cudaError_t e = cudaSuccess;
@@ -260,13 +262,15 @@ static haar_status_t shade_impl(haar_shift_plan_t p, const haar_transport_desc_t
       return launch_shade_gcsr_f32((const float*)t->vals, (const uint16_t*)t->idx, t->rowptr, t->V, (const float*)L,
                                    p->K, ncols, R, p->status, st);
     case HAAR_T_BINCSR_F16_U32:
-      if (ot != HAAR_OUT_F32 || lay != HAAR_LAYOUT_SKC)
-        return set_error(HAAR_ERR_UNSUPPORTED, "%s: BINCSR_F16_U32 needs F32 lighting in SKC layout", who);
+      if (ot != HAAR_OUT_F32 || (lay != HAAR_LAYOUT_SKC && lay != HAAR_LAYOUT_SKC4))
+        return set_error(HAAR_ERR_UNSUPPORTED, "%s: BINCSR_F16_U32 needs F32 lighting in SKC or SKC4 layout", who);
+      if (lay == HAAR_LAYOUT_SKC4 && !aligned(L, 16))
+        return set_error(HAAR_ERR_INVALID_ARG, "%s: SKC4 lighting must be 16-byte aligned", who);
       if (C > 4) return set_error(HAAR_ERR_UNSUPPORTED, "%s: BINCSR supports at most 4 channels", who);
       if (t->bins < 1 || t->bins > 255 || t->K < 1 || t->idx == nullptr || t->bin_of == nullptr)
         return set_error(HAAR_ERR_INVALID_ARG, "%s: BINCSR needs 1..255 bins, K >= 1, idx and bin_of", who);
       return launch_shade_bincsr_f16((const __half*)t->vals, (const uint32_t*)t->idx, t->bin_of, t->V, t->bins,
-                                     t->K, S, C, (const float*)L, p->K, R, st);
+                                     t->K, S, C, (const float*)L, p->K, lay == HAAR_LAYOUT_SKC4, R, st);
     default:
       return set_error(HAAR_ERR_INVALID_ARG, "%s: unknown transport kind %d", who, t->kind);
   }

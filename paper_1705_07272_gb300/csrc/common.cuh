@@ -169,7 +169,7 @@ haar_status_t launch_shade_csr_f32(const float* vals, const uint16_t* idx, const
                                    int V, const float* L, int NL, int ncols, float* R, cudaStream_t st);
 haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,
                                       int V, int bins, int K, int S, int C, const float* L,
-                                      long long NL, float* R, cudaStream_t st);
+                                      long long NL, bool vec4, float* R, cudaStream_t st);
 haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, const int32_t* gptr, int V,
                                     const float* L, int NL, int ncols, float* R, int* status, cudaStream_t st);
 haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16_t* idx, const float* vals,

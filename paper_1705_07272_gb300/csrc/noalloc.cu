@@ -49,7 +49,7 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   if (d->kind < HAAR_SHIFT_TRANSLATE || d->kind > HAAR_SHIFT_ROTATE_EULER ||
       (d->boundary != HAAR_BOUNDARY_SPHERE && d->boundary != HAAR_BOUNDARY_TORUS) ||
       d->out_type < HAAR_OUT_F32 || d->out_type > HAAR_OUT_F16 || d->out_layout < HAAR_LAYOUT_SCK ||
-      d->out_layout > HAAR_LAYOUT_KSC)
+      d->out_layout > HAAR_LAYOUT_SKC4 || (d->out_layout == HAAR_LAYOUT_SKC4 && d->channels > 4))
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: unknown kind, boundary, out_type or out_layout");
   const long long N = (long long)H * W;
   if (d->out_coeffs < 0 || d->out_coeffs > N)

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(256) k_shade_csr_f32(const float* __restrict__
 // the row is sorted by coefficient index, so each warp-wide gather touches
 // neighbouring lighting rows L[s][k][c] (channels interleaved), NL
 // coefficients per (s, c).
+template <bool VEC4>
 __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restrict__ vals,
                                                           const uint32_t* __restrict__ idx,
                                                           const uint8_t* __restrict__ bin_of, int V,
@@ -140,17 +141,27 @@ __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restri
   const int v = (int)(warp / S), s = (int)(warp - (long long)v * S);
   const int b = __ldg(bin_of + (long long)s * V + v);
   const long long row = ((long long)v * bins + b) * K;
-  const float* Ls = L + (long long)s * NL * C;
+  const int cs = VEC4 ? 4 : C;                              // floats per coefficient
+  const float* Ls = L + (long long)s * NL * cs;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
   for (int j = lane; j < K; j += 32) {
     const long long k0 = __ldg(idx + row + j);
     const bool ok = k0 < NL;                                // out-of-range entries are ignored
     const float t = ok ? __half2float(vals[row + j]) : 0.0f;
-    const float* lk = Ls + (ok ? k0 : 0) * C;
+    const float* lk = Ls + (ok ? k0 : 0) * cs;
+    if (VEC4) {
+      // one 16-byte gather per entry; the pad channel is never accumulated
+      const float4 x = __ldg(reinterpret_cast<const float4*>(lk));
+      acc[0] = fmaf(t, x.x, acc[0]);
+      acc[1] = fmaf(t, x.y, acc[1]);
+      acc[2] = fmaf(t, x.z, acc[2]);
+      acc[3] = fmaf(t, x.w, acc[3]);
+    } else {
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
+      for (int c = 0; c < 4; ++c)
+        if (c < C) acc[c] = fmaf(t, __ldg(lk + c), acc[c]);
+    }
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -539,11 +550,13 @@ haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16
 
 haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,
                                       int V, int bins, int K, int S, int C, const float* L, long long NL,
-                                      float* R, cudaStream_t st) {
+                                      bool vec4, float* R, cudaStream_t st) {
   const long long threads = (long long)V * S * 32;
-  return cuda_check(launch_pdl(k_shade_bincsr_f16, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, vals,
-                              idx, bin_of, V, bins, K, S, C, L, NL, R),
-                    "k_shade_bincsr_f16 launch");
+  const dim3 grid((unsigned)((threads + 255) / 256));
+  const cudaError_t e =
+      vec4 ? launch_pdl(k_shade_bincsr_f16<true>, grid, dim3(256), 0, st, vals, idx, bin_of, V, bins, K, S, C, L, NL, R)
+           : launch_pdl(k_shade_bincsr_f16<false>, grid, dim3(256), 0, st, vals, idx, bin_of, V, bins, K, S, C, L, NL, R);
+  return cuda_check(e, "k_shade_bincsr_f16 launch");
 }
 
 haar_status_t launch_view_bins(int V, int S, int bins, const float* pos, const float* nrm,

@@ -1275,6 +1275,7 @@ haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, 
   switch (p->desc.out_layout) {
     case HAAR_LAYOUT_SCK: a.st_s = C * K; a.st_c = K; a.st_k = 1; break;
     case HAAR_LAYOUT_SKC: a.st_s = K * C; a.st_c = 1; a.st_k = C; break;
+    case HAAR_LAYOUT_SKC4: a.st_s = K * 4; a.st_c = 1; a.st_k = 4; break;
     default: a.st_s = C; a.st_c = 1; a.st_k = (long long)S * C; break;
   }
   a.plane = (long long)S * C * K;

@@ -262,3 +262,8 @@ def test_bincsr_small(hs):
     ok = (margin > 1e-5).T
     assert rel_l2(got[ok], ref[ok]) <= 2e-3
     assert rel_l2(got[ok], ref[ok]) <= 1e-4
+    # the same frame with the lighting in SKC4 (16-byte gathers): identical sums
+    plan4 = hs.Plan(H, W, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_layout=hs.HAAR_LAYOUT_SKC4)
+    R4 = hs.shade_batch(plan4, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
+    assert torch.equal(R4, R)
+    assert plan4.status() == 0

@@ -38,7 +38,9 @@ def _run(hs, coeffs, H, W, kind, params, boundary=SPH, out_type=0, layout=0, K=0
         o = o[0] + o[1]
     else:
         raw = out.cpu()
-    if layout == hs.HAAR_LAYOUT_SKC:
+    if layout == hs.HAAR_LAYOUT_SKC4:
+        o = o[..., :C].transpose(0, 2, 1)
+    elif layout == hs.HAAR_LAYOUT_SKC:
         o = o.transpose(0, 2, 1)
     elif layout == hs.HAAR_LAYOUT_KSC:
         o = o.transpose(1, 2, 0)
@@ -69,7 +71,7 @@ def test_layouts_and_truncation_agree(hs, C, S):
     prm = np.stack([rng.uniform(-W, W, S), rng.uniform(-H, H, S)], axis=1)
     prm[:3] = [[3.3, 1.7], [100.25, 40.5], [7.0, 0.0]][:S]
     base, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_SCK)
-    for lay in (hs.HAAR_LAYOUT_SKC, hs.HAAR_LAYOUT_KSC):
+    for lay in (hs.HAAR_LAYOUT_SKC, hs.HAAR_LAYOUT_KSC, hs.HAAR_LAYOUT_SKC4):
         o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, lay)
         assert np.array_equal(o, base)
     for K in (1000, 7):
