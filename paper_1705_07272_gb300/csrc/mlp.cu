@@ -417,20 +417,34 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ y
 }
 
 // db[n] = sum_b dz[b][n]
-__global__ void k_colsum(const __nv_bfloat16* __restrict__ dz, int B, int N, float* __restrict__ db) {
+// Bias gradients db[n] = sum_b dz[b][n] in two deterministic passes: block
+// (x, y) sums rows [y R, (y + 1) R) of 32 columns into part[y][n] (8 row
+// strides per column, then a fixed-order add), and one thread per column
+// adds the P parts in order.
+__global__ void k_colsum_part(const __nv_bfloat16* __restrict__ dz, int B, int N, int R, float* __restrict__ part) {
   const int n = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int part = threadIdx.x >> 5, parts = blockDim.x >> 5;
+  const int sub = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * R, r1 = min(B, r0 + R);
   float acc = 0.0f;
   if (n < N)
-    for (int b = part; b < B; b += parts) acc += __bfloat162float(dz[(long long)b * N + n]);
+#pragma unroll 4
+    for (int b = r0 + sub; b < r1; b += 8) acc += __bfloat162float(dz[(long long)b * N + n]);
   __shared__ float red[8][32];
-  red[part][threadIdx.x & 31] = acc;
+  red[sub][threadIdx.x & 31] = acc;
   __syncthreads();
-  if (part == 0 && n < N) {
-    float s = 0.0f;
-    for (int p = 0; p < parts; ++p) s += red[p][threadIdx.x & 31];
-    db[n] = s;
+  if (sub == 0 && n < N) {
+    float t = 0.0f;
+    for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x & 31];
+    part[(long long)blockIdx.y * N + n] = t;
   }
+}
+
+__global__ void k_colsum_final(const float* __restrict__ part, int P, int N, float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float t = 0.0f;
+  for (int q = 0; q < P; ++q) t += part[(long long)q * N + n];
+  db[n] = t;
 }
 
 // One Adam step; the step count lives on the device (read here, advanced by
@@ -958,6 +972,18 @@ static EpiArgs epi(int M, int N) {
   return e;
 }
 
+// db = column sums of dz [B][N] through the partial-sum scratch ws (at least
+// 64 N floats; the split-K scratch, free between the weight-gradient GEMMs)
+static haar_status_t colsum(const __nv_bfloat16* dz, int B, int N, float* ws, float* db, cudaStream_t st) {
+  const int P = B >= 64 * 128 ? 64 : (B + 127) / 128 > 0 ? (B + 127) / 128 : 1;
+  const int R = (B + P - 1) / P;
+  k_colsum_part<<<dim3((N + 31) / 32, P), 256, 0, st>>>(dz, B, N, R, ws);
+  const haar_status_t r = cuda_check(cudaGetLastError(), "k_colsum_part launch");
+  if (r != HAAR_OK) return r;
+  k_colsum_final<<<(N + 255) / 256, 256, 0, st>>>(ws, P, N, db);
+  return cuda_check(cudaGetLastError(), "k_colsum_final launch");
+}
+
 static haar_status_t transpose(const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out, cudaStream_t st) {
   dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
   k_transpose<<<grid, block, 0, st>>>(in, R, C, out);
@@ -1006,8 +1032,7 @@ static haar_status_t backward(haar_mlp_s* M, int B, const float* target, cudaStr
     e.split_ws_floats = M->split_ws_floats;
     HS_TRY(gemm<EPI_F32>(M->tA, N_OUT, M->tB, WIDTH, B, e, M->status, st));
   }
-  k_colsum<<<(N_OUT + 31) / 32, 256, 0, st>>>(M->dout, B, N_OUT, M->g + b_off(4));
-  HS_TRY(cuda_check(cudaGetLastError(), "k_colsum launch"));
+  HS_TRY(colsum(M->dout, B, N_OUT, M->split_ws, M->g + b_off(4), st));
   {
     EpiArgs e = epi(B, WIDTH);
     e.out_bf16 = M->dz;
@@ -1029,8 +1054,7 @@ static haar_status_t backward(haar_mlp_s* M, int B, const float* target, cudaStr
     e.split_ws = M->split_ws;
     e.split_ws_floats = M->split_ws_floats;
     HS_TRY(gemm<EPI_F32>(M->tA, WIDTH, M->tB, fin, B, e, M->status, st));
-    k_colsum<<<(WIDTH + 31) / 32, 256, 0, st>>>(dz, B, WIDTH, M->g + b_off(l));
-    HS_TRY(cuda_check(cudaGetLastError(), "k_colsum launch"));
+    HS_TRY(colsum(dz, B, WIDTH, M->split_ws, M->g + b_off(l), st));
     if (l > 0) {
       EpiArgs d = epi(B, WIDTH);
       d.out_bf16 = dz_next;
