@@ -290,6 +290,55 @@ def measure_rows(hs, dev, flush, only=None):
         plan.close()
         del out
 
+    # coefficient-count sweep (the paper's other accuracy / cost knob): the c1
+    # frame shaded from the top-K transport, K = 4 .. 256 (group CSR), time and
+    # rel-L2 of the radiance against the untruncated double product on 512
+    # sampled vertices
+    if want("coefficient_count_sweep"):
+        sc1 = synth.scene(1)
+        H, W, C, S, V = sc1["H"], sc1["W"], sc1["C"], sc1["S"], sc1["V"]
+        Lc = hs.haar_forward(torch.tensor(sc1["light"], dtype=torch.float32, device=dev)).contiguous()
+        prm = torch.tensor(sc1["params"], dtype=torch.float64, device=dev)
+        Kmax = 256
+        order = torch.empty((V, Kmax), dtype=torch.int64, device=dev)      # by decreasing |T|
+        ordv = torch.empty((V, Kmax), dtype=torch.float32, device=dev)
+        pick = torch.tensor(np.sort(np.random.default_rng(11).choice(V, 512, replace=False)), device=dev)
+        dense_pick = torch.empty((512, H * W), dtype=torch.float64, device=dev)
+        for v0 in range(0, V, 4096):
+            v1 = min(V, v0 + 4096)
+            w = synth.transport_weights(sc1["pos"][v0:v1], sc1["nrm"][v0:v1], sc1["occ_c"], sc1["occ_r"], H, W,
+                                        device=dev, dtype=torch.float32, chunk=2048).contiguous()
+            T = hs.haar_forward(w)
+            top = torch.topk(T.abs(), Kmax, dim=1, sorted=True).indices
+            order[v0:v1] = top
+            ordv[v0:v1] = torch.gather(T, 1, top)
+            sel = (pick >= v0) & (pick < v1)
+            if bool(sel.any()):
+                dense_pick[sel] = T[pick[sel] - v0].double()
+            del w, T
+        plan = hs.Plan(H, W, C, max_shifts=S, out_layout=hs.HAAR_LAYOUT_KSC)
+        lit = torch.empty(plan.out_shape(S), dtype=torch.float32, device=dev)
+        hs.haar_shift(plan, Lc, prm, lit)
+        Ld = lit.double().reshape(H * W, S * C)
+        exact = (dense_pick @ Ld).reshape(512, S, C)
+        R = torch.empty((V, S, C), dtype=torch.float32, device=dev)
+        sweep = []
+        for K in (4, 8, 16, 32, 64, 128, 256):
+            idx, perm = torch.sort(order[:, :K], dim=1)
+            vals = torch.gather(ordv[:, :K], 1, perm).reshape(-1).contiguous()
+            rowptr = (torch.arange(V + 1, device=dev, dtype=torch.int64) * K).to(torch.int32)
+            idx16 = idx.to(torch.int32).to(torch.int16).reshape(-1).contiguous()
+            tr = hs.haar_transport_group(V, H * W, rowptr, idx16, vals)
+            ms = _timeit(lambda: hs.shade_vertices(plan, tr, lit, S, R), 10, flush, stream)
+            err = float(((R[pick].double() - exact).norm() / exact.norm()).item())
+            sweep.append({"K": K, "shade_ms": ms, "rel_l2_vs_untruncated": err})
+            del tr, vals, idx16
+        rows["coefficient_count_sweep"] = {"what": "c1 frame shaded from top-K transport (4-vertex group CSR), "
+                                                   "error against the untruncated double product (512 vertices)",
+                                           "levels": sweep}
+        plan.close()
+        del order, ordv, dense_pick
+
     # start-level sweep (the paper's accuracy / cost knob): the 64 c2 rotations of
     # RGB 256x512 started at level k = 0..3, time and rel-L2 of the N/4^k
     # coarsest coefficients against the full-map shift's
