@@ -70,8 +70,15 @@ typedef enum {
 typedef enum {
   HAAR_SHIFT_TRANSLATE = 0,   /* params [S][2] float64: (dx, dy) in pixels */
   HAAR_SHIFT_ROTATE = 1,      /* params [S][9] float64: R row-major, p' = R p */
-  HAAR_SHIFT_ROTATE_EULER = 2 /* params [S][3] float64: (alpha, beta, gamma),
+  HAAR_SHIFT_ROTATE_EULER = 2, /* params [S][3] float64: (alpha, beta, gamma),
                                  R = Rz(gamma) Ry(beta) Rx(alpha) (Eq. tRot) */
+  HAAR_SHIFT_ROTATE_CHAIN = 3  /* params as ROTATE_EULER; the paper's own route, an
+                                 approximation: the rotated map's finest derivative
+                                 fields by the chain rule (Eq. pde1-pde3, the mixed
+                                 term's second-order rule completed) and the detail
+                                 coefficients from them by Eq. conv / tker / sker;
+                                 float32 output only; the plan holds C x 4 x N floats
+                                 of fields per shift */
 } haar_shift_kind_t;
 
 typedef enum { HAAR_BOUNDARY_SPHERE = 0, HAAR_BOUNDARY_TORUS = 1 } haar_boundary_t;

@@ -27,6 +27,7 @@ HAAR_ERR_NOMEM = 6
 HAAR_SHIFT_TRANSLATE = 0
 HAAR_SHIFT_ROTATE = 1
 HAAR_SHIFT_ROTATE_EULER = 2
+HAAR_SHIFT_ROTATE_CHAIN = 3
 # haar_boundary_t
 HAAR_BOUNDARY_SPHERE = 0
 HAAR_BOUNDARY_TORUS = 1

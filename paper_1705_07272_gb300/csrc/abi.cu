@@ -54,6 +54,7 @@ static void free_plan(haar_shift_plan_s* p) {
   cudaFree(p->counters);
   cudaFree(p->light);
   cudaFree(p->status);
+  cudaFree(p->chain_ws);
   delete p;
 }
 
@@ -83,8 +84,10 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: width %d must be height or 2*height", d->width);
   if (d->channels < 1 || d->channels > 64)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: channels %d not in [1, 64]", d->channels);
-  if (d->kind < HAAR_SHIFT_TRANSLATE || d->kind > HAAR_SHIFT_ROTATE_EULER)
+  if (d->kind < HAAR_SHIFT_TRANSLATE || d->kind > HAAR_SHIFT_ROTATE_CHAIN)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: unknown kind %d", d->kind);
+  if (d->kind == HAAR_SHIFT_ROTATE_CHAIN && d->out_type != HAAR_OUT_F32)
+    return set_error(HAAR_ERR_UNSUPPORTED, "haar_shift_plan: ROTATE_CHAIN writes float32 only");
   if (d->boundary != HAAR_BOUNDARY_SPHERE && d->boundary != HAAR_BOUNDARY_TORUS)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: unknown boundary %d", d->boundary);
   if (d->max_shifts < 1 || d->max_shifts > 65535)
@@ -128,6 +131,8 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
   if (e == cudaSuccess) e = cudaMalloc(&p->counters, sizeof(unsigned) * S);
   if (e == cudaSuccess) e = cudaMalloc(&p->light, light_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int) * 4);
+  if (e == cudaSuccess && d->kind == HAAR_SHIFT_ROTATE_CHAIN)
+    e = cudaMalloc(&p->chain_ws, sizeof(float) * chain_ws_floats(g, (int)S));
   if (e != cudaSuccess) {
     free_plan(p);
     return set_error(HAAR_ERR_NOMEM, "haar_shift_plan: workspace allocation failed: %s", cudaGetErrorString(e));
@@ -185,6 +190,7 @@ haar_status_t haar_shift(haar_shift_plan_t p, const float* cin, const double* pa
   cudaStream_t st = (cudaStream_t)stream;
   r = launch_setup(p, cin, params, S, st);
   if (r != HAAR_OK) return r;
+  if (p->desc.kind == HAAR_SHIFT_ROTATE_CHAIN) return launch_chain(p, params, S, out, st);
   return launch_shift(p, cin, S, out, st);
 }
 
@@ -291,7 +297,8 @@ haar_status_t shade_batch(haar_shift_plan_t p, const float* cin, const double* p
   cudaStream_t st = (cudaStream_t)stream;
   r = launch_setup(p, cin, params, S, st);
   if (r != HAAR_OK) return r;
-  r = launch_shift(p, cin, S, p->light, st);
+  r = (p->desc.kind == HAAR_SHIFT_ROTATE_CHAIN) ? launch_chain(p, params, S, p->light, st)
+                                                : launch_shift(p, cin, S, p->light, st);
   if (r != HAAR_OK) return r;
   return shade_impl(p, t, p->light, S, R, st, "shade_batch");
 }

@@ -77,6 +77,7 @@ struct haar_shift_plan_s {
   void* light;               // shade_batch lighting [max_shifts * C * K] (x2 planes for BF16_HILO)
   size_t light_elems;        // elements per plane
   int* status;               // device status word (0 = fine)
+  float* chain_ws;           // ROTATE_CHAIN: [max_shifts][C][4][N] derivative fields, rotations, angle tables
 };
 
 namespace hs {
@@ -154,6 +155,9 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
                            cudaStream_t st);
 haar_status_t launch_trig(haar_shift_plan_s* p, cudaStream_t st);
+haar_status_t launch_chain(haar_shift_plan_s* p, const double* params, int S, void* out,
+                           cudaStream_t st);                                           // chain.cu
+size_t chain_ws_floats(const Geometry& g, int S);                                      // chain.cu
 bool ksc_eligible(const haar_shift_desc_t& d, const Geometry& g, int S);
 size_t ksc_means_floats(const Geometry& g, int S);
 size_t ksc_smem_floats(long long n16);

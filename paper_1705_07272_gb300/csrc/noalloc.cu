@@ -46,6 +46,8 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
                      d->start_level);
   const int H = d->height >> d->start_level, W = d->width >> d->start_level;   // the map the shift runs on
   if (C < 1 || C > 64) return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: channels %d not in [1, 64]", C);
+  if (d->kind == HAAR_SHIFT_ROTATE_CHAIN)
+    return set_error(HAAR_ERR_UNSUPPORTED, "haar_shift_noalloc: ROTATE_CHAIN needs a plan (field workspace)");
   if (d->kind < HAAR_SHIFT_TRANSLATE || d->kind > HAAR_SHIFT_ROTATE_EULER ||
       (d->boundary != HAAR_BOUNDARY_SPHERE && d->boundary != HAAR_BOUNDARY_TORUS) ||
       d->out_type < HAAR_OUT_F32 || d->out_type > HAAR_OUT_F16 || d->out_layout < HAAR_LAYOUT_SCK ||

@@ -1,0 +1,86 @@
+"""GPU parity of the paper's chain-rule rotation route (HAAR_SHIFT_ROTATE_CHAIN)
+against its FP64 oracle restatement (oracle.chain_rule), through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import chain_rule, haar as oh, resample, shift as osh
+from tests.helpers import f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(hs, c, H, W, eul, layout=0, K=0, boundary=0, start_level=0):
+    import torch
+    C = c.shape[0]
+    plan = hs.Plan(H, W, C, kind=hs.HAAR_SHIFT_ROTATE_CHAIN, boundary=boundary, max_shifts=len(eul),
+                   out_coeffs=K, out_layout=layout, start_level=start_level)
+    out = hs.haar_shift(plan, torch.tensor(c, dtype=torch.float32, device="cuda"),
+                        torch.tensor(np.asarray(eul, dtype=np.float64), device="cuda"))
+    o = out.double().cpu().numpy()
+    if layout == hs.HAAR_LAYOUT_SKC:
+        o = o.transpose(0, 2, 1)
+    assert plan.status() == 0
+    plan.close()
+    return o
+
+
+def _oracle(c, H, W, eul, boundary=0):
+    P = oh.inverse(c, H, W)
+    return np.stack([np.stack([chain_rule.rotate_coeffs(P[ch], resample.euler_matrix(*e), boundary)
+                               for ch in range(c.shape[0])]) for e in eul])
+
+
+def test_azimuth_rotation_is_the_exact_shift(hs):
+    H, W = 32, 64
+    c = f32(oh.forward(synth.lighting_pixels(np.random.default_rng(1), 3, H, W)))
+    eul = np.array([[0.0, 0.37, 0.0], [0.0, -2.0, 0.0]])
+    got = _run(hs, c, H, W, eul)
+    ref = osh.haar_shift(c, H, W, osh.ROTATE_EULER, eul)
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
+
+
+@pytest.mark.parametrize("H,W,boundary", [(32, 64, 0), (64, 128, 0), (32, 64, 1), (16, 16, 0)])
+def test_chain_rule_matches_oracle(hs, H, W, boundary):
+    c = f32(oh.forward(synth.lighting_pixels(np.random.default_rng(H), 3, H, W)))
+    eul = synth.euler_angles(np.random.default_rng(7), 4)
+    got = _run(hs, c, H, W, eul, boundary=boundary)
+    ref = _oracle(c, H, W, eul, boundary)
+    err = rel_l2(got, ref, axis=(1, 2))
+    print("chain-rule parity rel-L2 per rotation", err)
+    # float32 coordinates with the near-pole refinement move the result by
+    # <= 1.1e-6 (tests/test_chain_fp32_budget.py); the bound is the FP32 bar
+    assert err.max() <= 1e-5
+
+
+def test_layouts_and_truncation(hs):
+    H, W = 32, 64
+    c = f32(oh.forward(synth.lighting_pixels(np.random.default_rng(3), 3, H, W)))
+    eul = synth.euler_angles(np.random.default_rng(8), 3)
+    base = _run(hs, c, H, W, eul)
+    assert np.array_equal(_run(hs, c, H, W, eul, layout=1), base)
+    assert np.array_equal(_run(hs, c, H, W, eul, K=300), base[..., :300])
+
+
+def test_start_level(hs):
+    # the route on the level-1 scaling image (its N / 4 coarsest coefficients)
+    H, W = 64, 128
+    c = f32(oh.forward(synth.lighting_pixels(np.random.default_rng(5), 3, H, W)))
+    eul = synth.euler_angles(np.random.default_rng(9), 3)
+    got = _run(hs, c, H, W, eul, start_level=1)
+    ref = _oracle(c[:, :(H * W) >> 2], H >> 1, W >> 1, eul)
+    assert got.shape == ref.shape
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
+
+
+def test_pole_on_a_difference_midpoint(hs):
+    # Rx(alpha) with alpha the polar angle of row 3's lower edge sends the
+    # midpoint (row 2 + 1/2, column W / 2 - 1/2) onto the pole, where the route
+    # sets the Jacobian to 0
+    H, W = 32, 64
+    c = f32(oh.forward(synth.lighting_pixels(np.random.default_rng(11), 3, H, W)))
+    eul = np.array([[3.0 * np.pi / H, 0.0, 0.0], [-3.0 * np.pi / H, 0.0, 0.0]])
+    got = _run(hs, c, H, W, eul)
+    ref = _oracle(c, H, W, eul)
+    assert np.isfinite(got).all()
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
