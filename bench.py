@@ -362,6 +362,53 @@ def measure_rows(hs, dev, flush, only=None):
         rows["start_level_sweep"] = {"what": "64 rotations of RGB 256x512 started at level k (Sec. Algorithmic "
                                              "optimization), FP32", "levels": sweep}
 
+    # the paper's own rotation route (chain rule on the finest derivative fields,
+    # Eq. pde1-pde3, then Eq. conv/tker/sker) beside the exact operator: time for
+    # the 64 c2 rotations of RGB 256x512, and its accuracy as PSNR against the
+    # exact rotation (the synthetic analogue of Tables 1-4, at the paper's
+    # levels 5 and 6 and at 256x512) on two kinds of map: a band-limited one
+    # (smooth at the poles, like a measured environment's low frequencies) and
+    # the per-pixel lognormal map of the c2 scene.  PSNR = 10 log10(peak^2 /
+    # MSE) with the source map's peak and the per-pixel MSE (the transform is
+    # orthonormal, so it is the coefficient MSE), averaged over the rotations
+    if want("chain_rule_rotation"):
+        sc2 = synth.scene(2, V=1)
+        eul = torch.tensor(sc2["params"], dtype=torch.float64, device=dev)
+        S = eul.shape[0]
+        acc = []
+        for lvl, (H, W), kind in ((5, (32, 64), "smooth"), (6, (64, 128), "smooth"), (8, (256, 512), "smooth"),
+                                  (5, (32, 64), "lognormal"), (6, (64, 128), "lognormal"),
+                                  (8, (256, 512), "lognormal")):
+            if kind == "smooth":
+                light = synth.smooth_lighting(synth.rng_for(2, 30 + lvl), 3, H, W)
+            elif H != 256:
+                light = synth.lighting_pixels(synth.rng_for(2, 20 + lvl), 3, H, W)
+            else:
+                light = sc2["light"]
+            Lm = hs.haar_forward(torch.tensor(light, dtype=torch.float32, device=dev))
+            pe = hs.Plan(H, W, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S)
+            pc = hs.Plan(H, W, 3, kind=hs.HAAR_SHIFT_ROTATE_CHAIN, max_shifts=S)
+            oe = torch.empty(pe.out_shape(S), dtype=torch.float32, device=dev)
+            oc = torch.empty(pc.out_shape(S), dtype=torch.float32, device=dev)
+            hs.haar_shift(pe, Lm, eul, oe)
+            hs.haar_shift(pc, Lm, eul, oc)
+            mse = ((oc.double() - oe.double()) ** 2).mean(dim=(1, 2))
+            peak = float(np.max(light))
+            psnr = (10.0 * torch.log10(peak * peak / mse)).cpu().numpy()
+            rel = ((oc.double() - oe.double()).norm(dim=(1, 2)) / oe.double().norm(dim=(1, 2))).cpu().numpy()
+            row = {"level": lvl, "map": f"{H}x{W} {kind}", "psnr_db_mean": float(psnr.mean()),
+                   "psnr_db_min": float(psnr.min()), "rel_l2_mean": float(rel.mean()), "rel_l2_max": float(rel.max())}
+            if H == 256 and kind == "lognormal":
+                row["chain_ms"] = _timeit(lambda: hs.haar_shift(pc, Lm, eul, oc), 10, flush, stream)
+                row["exact_ms"] = _timeit(lambda: hs.haar_shift(pe, Lm, eul, oe), 10, flush, stream)
+            acc.append(row)
+            pe.close()
+            pc.close()
+            del oe, oc
+        rows["chain_rule_rotation"] = {"what": "64 rotations of RGB maps by the paper's chain-rule route "
+                                               "(HAAR_SHIFT_ROTATE_CHAIN) against the exact operator, FP32",
+                                       "levels": acc}
+
     # c2 frame: 64 rotations -> bf16 hi/lo lowest 4096 -> tcgen05 contraction for 200k vertices
     if want("c2_dense_tc"):
         sc2 = synth.scene(2)

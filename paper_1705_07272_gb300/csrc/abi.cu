@@ -92,9 +92,11 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: unknown boundary %d", d->boundary);
   if (d->max_shifts < 1 || d->max_shifts > 65535)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: max_shifts %d not in [1, 65535]", d->max_shifts);
-  if (d->start_level < 0 || (d->height >> d->start_level) < 2)
+  if (d->start_level < 0 || d->start_level > 12 || (d->height >> d->start_level) < 2)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_plan: start_level %d leaves a map smaller than 2 x 2",
                      d->start_level);
+  if (d->kind == HAAR_SHIFT_ROTATE_CHAIN && (d->height >> d->start_level) < 16)
+    return set_error(HAAR_ERR_UNSUPPORTED, "haar_shift_plan: ROTATE_CHAIN needs a map of at least 16 rows");
   const int Hk = d->height >> d->start_level, Wk = d->width >> d->start_level;
   const long long N = (long long)Hk * Wk;          // coefficients of the map the shift runs on
   if (d->out_coeffs < 0 || d->out_coeffs > N)

@@ -87,6 +87,20 @@ def lighting_pixels(rng: np.random.Generator, C: int, H: int, W: int,
     return base + add[None]
 
 
+def smooth_lighting(rng: np.random.Generator, C: int, H: int, W: int, lobes: int = 4,
+                    kappa: float = 6.0, amp: float = 4.0) -> np.ndarray:
+    """Band-limited lat-long lighting map [C, H, W] (float64): 1 plus a few
+    broad lobes amp * exp(kappa (d . c - 1)) around random directions c, smooth
+    everywhere on the sphere, the poles included (a stand-in for a measured
+    environment map's low-frequency content)."""
+    d = pixel_directions(H, W)
+    out = np.ones((C, H, W))
+    for ch in range(C):
+        for c in uniform_sphere(rng, lobes):
+            out[ch] += amp * rng.uniform(0.5, 1.0) * np.exp(kappa * (d @ c - 1.0))
+    return out
+
+
 def sphere_vertices(rng: np.random.Generator, V: int):
     """Vertices uniform on the unit sphere; normal = position."""
     p = uniform_sphere(rng, V)

@@ -50,7 +50,7 @@ def _desc(lib, **kw):
                                  dict(channels=0), dict(channels=65), dict(kind=7), dict(boundary=2),
                                  dict(max_shifts=0), dict(out_coeffs=-1), dict(out_coeffs=32 * 64 + 1),
                                  dict(out_type=3), dict(out_layout=5), dict(height=8192, width=8192),
-                                 dict(start_level=-1), dict(start_level=5),
+                                 dict(start_level=-1), dict(start_level=5), dict(start_level=40),
                                  dict(start_level=2, out_coeffs=(32 * 64 >> 4) + 1)])
 def test_plan_rejects_bad_descriptors(lib, bad):
     h = ctypes.c_void_p()
@@ -58,6 +58,15 @@ def test_plan_rejects_bad_descriptors(lib, bad):
     assert st == lib.HAAR_ERR_INVALID_ARG
     assert h.value is None
     assert lib.lib().haar_last_error()
+
+
+@pytest.mark.parametrize("bad", [dict(out_type=1), dict(height=8, width=16), dict(start_level=2)])
+def test_chain_route_rejects_what_it_does_not_support(lib, bad):
+    # float32 output only; the tile kernel needs a map of at least 16 rows
+    h = ctypes.c_void_p()
+    st = lib.lib().haar_shift_plan(ctypes.byref(_desc(lib, kind=lib.HAAR_SHIFT_ROTATE_CHAIN, **bad)), ctypes.byref(h))
+    assert st == lib.HAAR_ERR_UNSUPPORTED
+    assert h.value is None
 
 
 def test_null_arguments(lib):
