@@ -409,6 +409,73 @@ def measure_rows(hs, dev, flush, only=None):
                                                "(HAAR_SHIFT_ROTATE_CHAIN) against the exact operator, FP32",
                                        "levels": acc}
 
+    # the paper's shading loop (N2): rotation input pass (normal -> record),
+    # rotation pass (each vertex's BRDF map rotated onto its normal by
+    # haar_shift) and triple integral pass (Tripling Coefficient Theorem) for
+    # the 50 000 c1 torus vertices, at the paper's levels 5 (32x64) and 6
+    # (64x128); the triple kernel is bound by reading each vertex's two rows
+    if want("triple_product_loop"):
+        sc1 = synth.scene(1)
+        V = sc1["V"]
+        nrm = torch.tensor(sc1["nrm"], dtype=torch.float32, device=dev)
+        levels = []
+        for lvl, (H, W) in ((5, (32, 64)), (6, (64, 128))):
+            N = H * W
+            light = hs.haar_forward(torch.tensor(synth.lighting_pixels(synth.rng_for(1, 40 + lvl), 3, H, W),
+                                                 dtype=torch.float32, device=dev))
+            brdf = hs.haar_forward(torch.tensor(synth.local_brdf_map(H, W)[None], dtype=torch.float32, device=dev))
+            vis = torch.empty((V, N), dtype=torch.float32, device=dev)
+            for v0 in range(0, V, 8192):
+                v1 = min(V, v0 + 8192)
+                w = synth.transport_weights(sc1["pos"][v0:v1], sc1["nrm"][v0:v1], sc1["occ_c"], sc1["occ_r"], H, W,
+                                            device=dev, dtype=torch.float32, chunk=4096, cosine=False).contiguous()
+                vis[v0:v1] = hs.haar_forward(w)
+                del w
+            plan = hs.Plan(H, W, 1, kind=hs.HAAR_SHIFT_ROTATE, max_shifts=V)
+            prm = torch.empty((V, 9), dtype=torch.float64, device=dev)
+            rot = torch.empty(plan.out_shape(V), dtype=torch.float32, device=dev)
+            out = torch.empty((V, 3), dtype=torch.float32, device=dev)
+            work = torch.empty(hs.haar_triple_work_floats(H, W, 3), dtype=torch.float32, device=dev)
+
+            work2 = torch.empty(hs.haar_shade_triple_work_floats(H, W, 3), dtype=torch.float32, device=dev)
+            brdf_l = brdf[0].contiguous()
+
+            def unfused():
+                hs.haar_normal_rotations(nrm, prm)
+                hs.haar_shift(plan, brdf, prm, rot)
+                hs.haar_triple_product(H, W, light, rot[:, 0, :], vis, out, work)
+
+            def fused():
+                hs.haar_normal_rotations(nrm, prm)
+                hs.haar_shade_triple(H, W, light, brdf_l, prm, vis, out, work2)
+
+            unfused()
+            ref_out = out.clone()
+            fused()
+            agree = float(((out - ref_out).norm() / ref_out.norm()).item())
+            ms_frame = _timeit(fused, 10, flush, stream)
+            ms_fused = _timeit(lambda: hs.haar_shade_triple(H, W, light, brdf_l, prm, vis, out, work2), 10, flush,
+                               stream)
+            ms_unfused = _timeit(unfused, 10, flush, stream)
+            ms_rot = _timeit(lambda: hs.haar_shift(plan, brdf, prm, rot), 10, flush, stream)
+            ms_tri = _timeit(lambda: hs.haar_triple_product(H, W, light, rot[:, 0, :], vis, out, work), 10, flush,
+                             stream)
+            byt = V * (2 * N + 3) * 4
+            byt_fused = V * (N + 3) * 4
+            levels.append({"level": lvl, "map": f"{H}x{W}", "frame_ms": ms_frame, "vertices_per_s": V / ms_frame * 1e3,
+                           "fused_kernel_ms": ms_fused, "fused_achieved_gbs": byt_fused / ms_fused / 1e6,
+                           "fused_bound": "alu (per-pixel rotation coordinates)",
+                           "unfused_frame_ms": ms_unfused, "unfused_rotation_ms": ms_rot, "triple_ms": ms_tri,
+                           "triple_achieved_gbs": byt / ms_tri / 1e6, "triple_frac_hbm": byt / ms_tri / 1e6 / hbm,
+                           "triple_algorithmic_bytes": byt, "fused_vs_unfused_rel_l2": agree})
+            plan.close()
+            del vis, rot
+        rows["triple_product_loop"] = {"what": "shading loop of 50 000 torus vertices: normal -> rotation record, "
+                                               "Lambertian BRDF map rotated per vertex, RGB triple product with "
+                                               "per-vertex visibility, FP32; frame = the fused kernel "
+                                               "(haar_shade_triple), unfused = haar_shift + haar_triple_product",
+                                       "levels": levels}
+
     # c2 frame: 64 rotations -> bf16 hi/lo lowest 4096 -> tcgen05 contraction for 200k vertices
     if want("c2_dense_tc"):
         sc2 = synth.scene(2)

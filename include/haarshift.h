@@ -264,6 +264,68 @@ HAAR_API haar_status_t haar_view_bins(int V, int S, int bins, const float* pos, 
                              void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The paper's shading loop (Sec. "Algorithmic optimization" and Sec.
+ * "Experimental results": rotation input pass, rotation pass, triple
+ * integral pass): each vertex's BRDF map, given in a local frame whose normal
+ * sits at the +y pole, is rotated onto the vertex normal with haar_shift
+ * (HAAR_SHIFT_ROTATE, parameters from haar_normal_rotations), then the
+ * outgoing radiance is the triple product of lighting x rotated BRDF x
+ * visibility (Sec. "Related work", Tripling Coefficient Theorem).
+ * ------------------------------------------------------------------------- */
+
+/* Rotation records of the rotation input pass: for normals [V][3] float32
+ * (normalised here) params [V][9] float64 receives R = Rx(-theta_N)
+ * Ry(-phi_N), row-major, theta_N = acos(n_y), phi_N = atan2(n_x, n_z): a tilt
+ * about the x axis and a shift along phi, with R N = +y.  As
+ * HAAR_SHIFT_ROTATE parameters (g(w) = f(R w)) it carries a local-frame map
+ * onto the normal.  A zero normal gives a NaN record. */
+HAAR_API haar_status_t haar_normal_rotations(int V, const float* normals, double* params, void* stream);
+
+/* Floats of the workspace haar_triple_product needs for C lighting channels
+ * of an H x W map (the lighting's mean over every Haar square, its details
+ * and mean packed per square, and a status word). */
+HAAR_API long long haar_triple_work_floats(int H, int W, int C);
+
+/* The Haar triple product of the triple integral pass:
+ *   out[v][c] = sum_ijk C_ijk light[c][i] brdf[v][j] vis[v][k]
+ * with the tripling coefficients of the orthonormal basis above (unit pixel
+ * measure: 1/H for three scaling functions, 1/B for the three distinct
+ * wavelet types on one square of side B, and for a repeated wavelet the value
+ * of the third basis function on its square), evaluated square by square in
+ * O(N) per vertex with the factors' means over each square.  This equals the
+ * pixel sum of the three reconstructed maps; fold the solid-angle weight
+ * sin(theta) dtheta dphi into one factor (visibility) for the integral over
+ * the sphere.
+ *   light: [C][N] float32, 1 <= C <= 4;  brdf, vis: row v at brdf + v *
+ *   brdf_stride (floats), canonical order, 16-byte aligned rows (strides a
+ *   multiple of 4); out: [V][C] float32; work: haar_triple_work_floats(H, W,
+ *   C) floats, 16-byte aligned.  Needs N = H W <= 8192 (both factors of a
+ *   vertex are staged in shared memory by bulk copies).  After the call, the
+ *   int at work[0] is 0, or has bit HAAR_ERR_TIMEOUT set if a bulk copy did
+ *   not complete within 2 s (that vertex's outputs are then NaN). */
+HAAR_API haar_status_t haar_triple_product(int H, int W, int C, int V, const float* light, const float* brdf,
+                                           long long brdf_stride, const float* vis, long long vis_stride,
+                                           float* out, float* work, void* stream);
+
+/* Floats of the workspace haar_shade_triple needs (lighting means, the
+ * BRDF's pixel map, angle tables and a status word). */
+HAAR_API long long haar_shade_triple_work_floats(int H, int W, int C);
+
+/* The rotation pass and the triple integral pass fused, one CTA per vertex:
+ *   out[v][c] = sum_ijk C_ijk light[c][i] b_v[j] vis[v][k],
+ * b_v = the coefficients of the local-frame BRDF map brdf_local [N] after the
+ * rotation record params[v] (HAAR_SHIFT_ROTATE semantics, SPHERE boundary:
+ * g(w) = f(R w), bilinear).  The same result as haar_shift (one channel, one
+ * shift per vertex) followed by haar_triple_product, without writing the
+ * rotated BRDF to memory.  light: [C][N]; params: [V][9] float64 (e.g. from
+ * haar_normal_rotations); vis rows as in haar_triple_product; out: [V][C];
+ * work: haar_shade_triple_work_floats(H, W, C) floats, 16-byte aligned, the
+ * int at work[0] the status word as in haar_triple_product.  N <= 8192. */
+HAAR_API haar_status_t haar_shade_triple(int H, int W, int C, int V, const float* light, const float* brdf_local,
+                                         const double* params, const float* vis, long long vis_stride, float* out,
+                                         float* work, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Transport surrogate (not in the paper; a learned stand-in for stored
  * transport).  A 4 x 256 GELU MLP (tanh-form GELU) maps a vertex's position, normal and view
  * direction to its transport coefficients at a fixed set of 512 canonical

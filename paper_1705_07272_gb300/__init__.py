@@ -53,7 +53,8 @@ EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_for
            "haar_last_error", "haar_version", "haar_mlp_param_count", "haar_mlp_create",
            "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params", "haar_mlp_forward",
            "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status",
-           "haar_shift_noalloc", "haar_transport_group", "haar_shift_plan_status")
+           "haar_shift_noalloc", "haar_transport_group", "haar_shift_plan_status", "haar_normal_rotations",
+           "haar_triple_work_floats", "haar_triple_product", "haar_shade_triple_work_floats", "haar_shade_triple")
 
 
 class HaarShiftDesc(ctypes.Structure):
@@ -100,6 +101,16 @@ def lib() -> ctypes.CDLL:
     L.haar_transport_group.restype = st
     L.haar_shift_plan_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i]
     L.haar_shift_plan_status.restype = st
+    L.haar_normal_rotations.argtypes = [i, vp, vp, vp]
+    L.haar_normal_rotations.restype = st
+    L.haar_triple_work_floats.argtypes = [i, i, i]
+    L.haar_triple_work_floats.restype = ctypes.c_longlong
+    L.haar_triple_product.argtypes = [i, i, i, i, vp, vp, ctypes.c_longlong, vp, ctypes.c_longlong, vp, vp, vp]
+    L.haar_triple_product.restype = st
+    L.haar_shade_triple_work_floats.argtypes = [i, i, i]
+    L.haar_shade_triple_work_floats.restype = ctypes.c_longlong
+    L.haar_shade_triple.argtypes = [i, i, i, i, vp, vp, vp, vp, ctypes.c_longlong, vp, vp, vp]
+    L.haar_shade_triple.restype = st
     for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_shift_noalloc", "haar_forward", "haar_inverse",
                  "shade_vertices", "shade_batch", "haar_view_bins"):
         getattr(L, name).restype = st
@@ -321,6 +332,77 @@ def haar_view_bins(pos, nrm, cams, bin_dirs, out=None, stream=None):
     _check(lib().haar_view_bins(V, S, bins, _dev(pos, torch.float32, "pos"), _dev(nrm, torch.float32, "nrm"),
                                 _dev(cams, torch.float32, "cams"), _dev(bin_dirs, torch.float32, "bin_dirs"),
                                 _dev(out, torch.uint8, "bin_of"), _stream(stream)))
+    return out
+
+
+def haar_normal_rotations(normals, out=None, stream=None):
+    """Rotation records [V][9] float64 (HAAR_SHIFT_ROTATE parameters) that
+    carry a local-frame map (normal at the +y pole) onto each normal."""
+    import torch
+    V = normals.shape[0]
+    if out is None:
+        out = torch.empty((V, 9), dtype=torch.float64, device=normals.device)
+    _check(lib().haar_normal_rotations(V, _dev(normals, torch.float32, "normals"), _dev(out, torch.float64, "params"),
+                                       _stream(stream)))
+    return out
+
+
+def haar_triple_work_floats(H, W, C):
+    n = lib().haar_triple_work_floats(H, W, C)
+    if n < 0:
+        raise HaarError(HAAR_ERR_INVALID_ARG, f"no triple-product workspace for {H}x{W}, C={C}")
+    return n
+
+
+def haar_triple_product(H, W, light, brdf, vis, out=None, work=None, stream=None):
+    """out [V][C]: the Haar triple product of lighting [C][N] with each
+    vertex's BRDF row and visibility row ([V][>=N] float32, rows 16-byte aligned)."""
+    import torch
+    C, V = light.shape[0], brdf.shape[0]
+    if vis.shape[0] != V:
+        raise ValueError("brdf and vis need the same number of rows")
+    for name, t in (("brdf", brdf), ("vis", vis)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+            raise TypeError(f"{name} must be a float32 CUDA tensor")
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{name} must be [V][>=N] with unit column stride")
+    if out is None:
+        out = torch.empty((V, C), dtype=torch.float32, device=light.device)
+    if work is None:
+        work = torch.empty(haar_triple_work_floats(H, W, C), dtype=torch.float32, device=light.device)
+    _check(lib().haar_triple_product(H, W, C, V, _dev(light, torch.float32, "light"), brdf.data_ptr(),
+                                     brdf.stride(0), vis.data_ptr(), vis.stride(0), _dev(out, torch.float32, "out"),
+                                     _dev(work, torch.float32, "work"), _stream(stream)))
+    return out
+
+
+def haar_shade_triple_work_floats(H, W, C):
+    n = lib().haar_shade_triple_work_floats(H, W, C)
+    if n < 0:
+        raise HaarError(HAAR_ERR_INVALID_ARG, f"no shading-loop workspace for {H}x{W}, C={C}")
+    return n
+
+
+def haar_shade_triple(H, W, light, brdf_local, params, vis, out=None, work=None, stream=None):
+    """out [V][C]: the rotation pass and the triple product fused; light [C][N],
+    brdf_local [N] (local frame), params [V][9] float64 rotation records,
+    vis [V][>=N] float32 rows (16-byte aligned)."""
+    import torch
+    C, V = light.shape[0], params.shape[0]
+    if vis.shape[0] != V:
+        raise ValueError("params and vis need the same number of rows")
+    if not isinstance(vis, torch.Tensor) or not vis.is_cuda or vis.dtype != torch.float32:
+        raise TypeError("vis must be a float32 CUDA tensor")
+    if vis.dim() != 2 or vis.stride(1) != 1:
+        raise ValueError("vis must be [V][>=N] with unit column stride")
+    if out is None:
+        out = torch.empty((V, C), dtype=torch.float32, device=light.device)
+    if work is None:
+        work = torch.empty(haar_shade_triple_work_floats(H, W, C), dtype=torch.float32, device=light.device)
+    _check(lib().haar_shade_triple(H, W, C, V, _dev(light, torch.float32, "light"),
+                                   _dev(brdf_local, torch.float32, "brdf_local"), _dev(params, torch.float64, "params"),
+                                   vis.data_ptr(), vis.stride(0), _dev(out, torch.float32, "out"),
+                                   _dev(work, torch.float32, "work"), _stream(stream)))
     return out
 
 

@@ -326,4 +326,72 @@ haar_status_t haar_view_bins(int V, int S, int bins, const float* pos, const flo
   return launch_view_bins(V, S, bins, pos, nrm, cams, bin_dirs, bin_of, (cudaStream_t)stream);
 }
 
+haar_status_t haar_normal_rotations(int V, const float* normals, double* params, void* stream) {
+  HS_ENTRY("haar_normal_rotations");
+  if (V < 0) return set_error(HAAR_ERR_INVALID_ARG, "haar_normal_rotations: V = %d", V);
+  if (V == 0) return HAAR_OK;
+  if (!normals || !params) return set_error(HAAR_ERR_INVALID_ARG, "haar_normal_rotations: null pointer");
+  if (!aligned(normals, 4) || !aligned(params, 8))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_normal_rotations: misaligned pointer");
+  return launch_normal_rotations(V, normals, params, (cudaStream_t)stream);
+}
+
+static bool triple_map_ok(int H, int W) { return is_pow2(H) && H >= 2 && (W == H || W == 2 * H); }
+
+long long haar_triple_work_floats(int H, int W, int C) {
+  if (!triple_map_ok(H, W) || (long long)H * W > 8192 || C < 1 || C > 4) return -1;
+  return triple_work_floats(H, W, C);
+}
+
+haar_status_t haar_triple_product(int H, int W, int C, int V, const float* light, const float* brdf,
+                                  long long brdf_stride, const float* vis, long long vis_stride, float* out,
+                                  float* work, void* stream) {
+  HS_ENTRY("haar_triple_product");
+  if (!triple_map_ok(H, W))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_triple_product: map %d x %d (H a power of two >= 2, W = H or 2H)",
+                     H, W);
+  const long long N = (long long)H * W;
+  if (N > 8192)
+    return set_error(HAAR_ERR_UNSUPPORTED, "haar_triple_product: N = %lld > 8192 (rows staged in shared memory)", N);
+  if (C < 1 || C > 4) return set_error(HAAR_ERR_INVALID_ARG, "haar_triple_product: C = %d not in [1, 4]", C);
+  if (V < 0) return set_error(HAAR_ERR_INVALID_ARG, "haar_triple_product: V = %d", V);
+  if (V == 0) return HAAR_OK;
+  if (!light || !brdf || !vis || !out || !work)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_triple_product: null pointer");
+  if (brdf_stride < N || vis_stride < N || brdf_stride % 4 || vis_stride % 4)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_triple_product: strides %lld, %lld (>= N, multiples of 4)",
+                     brdf_stride, vis_stride);
+  if (!aligned(brdf, 16) || !aligned(vis, 16) || !aligned(work, 16) || !aligned(light, 4) || !aligned(out, 4))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_triple_product: misaligned pointer");
+  return launch_triple(H, W, C, V, light, brdf, brdf_stride, vis, vis_stride, out, work, (cudaStream_t)stream);
+}
+
+long long haar_shade_triple_work_floats(int H, int W, int C) {
+  if (!triple_map_ok(H, W) || (long long)H * W > 8192 || C < 1 || C > 4) return -1;
+  return shade_triple_work_floats(H, W, C);
+}
+
+haar_status_t haar_shade_triple(int H, int W, int C, int V, const float* light, const float* brdf_local,
+                                const double* params, const float* vis, long long vis_stride, float* out,
+                                float* work, void* stream) {
+  HS_ENTRY("haar_shade_triple");
+  if (!triple_map_ok(H, W))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_triple: map %d x %d (H a power of two >= 2, W = H or 2H)", H, W);
+  const long long N = (long long)H * W;
+  if (N > 8192)
+    return set_error(HAAR_ERR_UNSUPPORTED, "haar_shade_triple: N = %lld > 8192 (rows staged in shared memory)", N);
+  if (C < 1 || C > 4) return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_triple: C = %d not in [1, 4]", C);
+  if (V < 0) return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_triple: V = %d", V);
+  if (V == 0) return HAAR_OK;
+  if (!light || !brdf_local || !params || !vis || !out || !work)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_triple: null pointer");
+  if (vis_stride < N || vis_stride % 4)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_triple: vis stride %lld (>= N, a multiple of 4)", vis_stride);
+  if (!aligned(vis, 16) || !aligned(work, 16) || !aligned(params, 8) || !aligned(light, 4) ||
+      !aligned(brdf_local, 4) || !aligned(out, 4))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_triple: misaligned pointer");
+  return launch_shade_triple(H, W, C, V, light, brdf_local, params, vis, vis_stride, out, work,
+                             (cudaStream_t)stream);
+}
+
 }  // extern "C"

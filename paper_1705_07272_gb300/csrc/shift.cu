@@ -44,28 +44,6 @@ struct ShiftArgs {
 
 // ------------------------------------------------------------------ helpers
 
-// atan2(y, x) in [-pi, pi] for the rotation coordinates: reduction to
-// t = min(|x|, |y|) / max(|x|, |y|) in [0, 1], atan(t) = t P(t^2) with P of
-// degree 7 (coefficients from a least-squares fit on [0, 1] reweighted
-// towards its largest errors: |error| < 1.5e-7 rad when evaluated in FP32,
-// i.e. < 2e-5 pixel at 512 columns), then the reflections atan(y/x) =
-// pi/2 - atan(x/y) and the half-plane x < 0.  (0, 0) gives 0.
-__device__ __forceinline__ float rot_atan2(float y, float x) {
-  const float ax = fabsf(x), ay = fabsf(y);
-  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-  const float t = (mx > 0.0f) ? __fdividef(mn, mx) : 0.0f;
-  const float u = t * t;
-  constexpr float P[8] = {9.999993443e-01f, -3.332985938e-01f, 1.994656622e-01f, -1.390863210e-01f, 9.642205387e-02f, -5.591243505e-02f, 2.186303213e-02f, -4.054587334e-03f};
-  float p = P[7];
-#pragma unroll
-  for (int i = 6; i >= 0; --i) p = fmaf(p, u, P[i]);
-  float r = t * p;
-  if (ay > ax) r = 1.57079632679f - r;
-  if (x < 0.0f) r = 3.14159265359f - r;
-  return copysignf(r, y);
-}
-
-
 __device__ __forceinline__ void ext_index(int& i, int& j, int H, int W, int boundary) {
   if (boundary == HAAR_BOUNDARY_TORUS) {
     i %= H;

@@ -101,6 +101,19 @@ def smooth_lighting(rng: np.random.Generator, C: int, H: int, W: int, lobes: int
     return out
 
 
+def local_brdf_map(H: int, W: int, expo: float = 0.0, view_theta: float = 0.0) -> np.ndarray:
+    """A cosine-weighted BRDF map [H, W] in the local frame (normal at the +y
+    pole): Lambertian cos / pi for expo = 0, else a normalised Phong lobe
+    (expo + 2) / (2 pi) max(0, r . w)^expo cos about the mirror direction r of
+    a view at polar angle view_theta in the phi = 0 half-plane."""
+    d = pixel_directions(H, W)
+    cos = np.maximum(d[..., 1], 0.0)
+    if expo <= 0.0:
+        return cos / math.pi
+    r = np.array([0.0, math.cos(view_theta), -math.sin(view_theta)])
+    return (expo + 2.0) / (2.0 * math.pi) * np.maximum(d @ r, 0.0) ** expo * cos
+
+
 def sphere_vertices(rng: np.random.Generator, V: int):
     """Vertices uniform on the unit sphere; normal = position."""
     p = uniform_sphere(rng, V)
@@ -202,12 +215,14 @@ def bin_view_world(nrm: np.ndarray, nbins: int = 16) -> np.ndarray:
 # ---------------------------------------------------------------- transport integrand
 
 def transport_weights(pos, nrm, occ_c, occ_r, Ht: int, Wt: int, *, view=None, expo=None,
-                      device="cpu", dtype=None, chunk: int = 256):
+                      device="cpu", dtype=None, chunk: int = 256, cosine: bool = True):
     """Midpoint-rule transport weights w[v, i, j] = t_v(d_ij) sin(theta_i) dtheta dphi
     on an Ht x Wt lat-long quadrature grid, as a torch tensor [V, Ht, Wt].
 
     ``view`` [V, 3] and ``expo`` [V] select the Phong integrand; otherwise the
-    diffuse one.  Evaluated in chunks of vertices with torch on ``device``."""
+    diffuse one; ``cosine=False`` (no view) leaves the visibility alone, for
+    the triple product's visibility factor.  Evaluated in chunks of vertices
+    with torch on ``device``."""
     import torch
     if dtype is None:
         dtype = torch.float64 if str(device) == "cpu" else torch.float32
@@ -229,7 +244,7 @@ def transport_weights(pos, nrm, occ_c, occ_r, Ht: int, Wt: int, *, view=None, ex
         v1 = min(V, v0 + chunk)
         n = nrm_t[v0:v1]
         cosn = n[:, 0:1] * dx + n[:, 1:2] * dy + n[:, 2:3] * dz
-        t = torch.clamp(cosn, min=0.0)
+        t = torch.clamp(cosn, min=0.0) if cosine else torch.ones_like(cosn)
         if view_t is not None:
             vv = view_t[v0:v1]
             ndv = (n * vv).sum(1, keepdim=True)

@@ -103,3 +103,56 @@ def test_binding_rejects_host_tensors(lib):
     import torch
     with pytest.raises(ValueError):
         lib._dev(torch.zeros(4), torch.float32, "x")
+
+
+@pytest.mark.parametrize("args,err", [
+    (dict(H=128, W=128), "UNSUPPORTED"),          # N > 8192
+    (dict(H=12, W=24), "INVALID_ARG"),
+    (dict(H=16, W=64), "INVALID_ARG"),
+    (dict(C=0), "INVALID_ARG"), (dict(C=5), "INVALID_ARG"), (dict(V=-1), "INVALID_ARG"),
+    (dict(sb=100), "INVALID_ARG"),                # shorter than N
+    (dict(sb=514), "INVALID_ARG"),                # not a multiple of 4
+    (dict(brdf=0x1008), "INVALID_ARG"),           # not 16-byte aligned
+    (dict(work=0x1004), "INVALID_ARG"),
+    (dict(light=0), "INVALID_ARG"),
+])
+def test_triple_product_rejects_bad_arguments(lib, args, err):
+    # validation happens before any launch, so fake device addresses suffice
+    a = dict(H=16, W=32, C=3, V=4, light=0x1000, brdf=0x2000, sb=512, vis=0x3000, sv=512, out=0x4000, work=0x5000)
+    a.update(args)
+    st = lib.lib().haar_triple_product(a["H"], a["W"], a["C"], a["V"], a["light"], a["brdf"], a["sb"], a["vis"],
+                                       a["sv"], a["out"], a["work"], None)
+    assert st == getattr(lib, "HAAR_ERR_" + err)
+    assert lib.lib().haar_last_error()
+
+
+def test_triple_work_size(lib):
+    # 4 status floats + C means over the (N - q) / 3 squares (rounded up to 4)
+    # + one float4 per square and channel
+    nm = (2048 - 2) // 3
+    assert lib.lib().haar_triple_work_floats(32, 64, 3) == 4 + ((3 * nm + 3) & ~3) + 4 * 3 * nm
+    assert lib.lib().haar_triple_work_floats(128, 128, 3) == -1
+    assert lib.lib().haar_triple_work_floats(32, 64, 5) == -1
+
+
+def test_normal_rotations_rejects_bad_arguments(lib):
+    L = lib.lib()
+    assert L.haar_normal_rotations(-1, 0x1000, 0x2000, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_normal_rotations(4, 0, 0x2000, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_normal_rotations(4, 0x1000, 0x2004, None) == lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_normal_rotations(0, 0, 0, None) == lib.HAAR_OK
+
+
+@pytest.mark.parametrize("args,err", [
+    (dict(H=128, W=128), "UNSUPPORTED"), (dict(H=16, W=64), "INVALID_ARG"), (dict(C=5), "INVALID_ARG"),
+    (dict(sv=510), "INVALID_ARG"), (dict(vis=0x3004), "INVALID_ARG"), (dict(params=0x6004), "INVALID_ARG"),
+    (dict(brdf=0), "INVALID_ARG"),
+])
+def test_shade_triple_rejects_bad_arguments(lib, args, err):
+    a = dict(H=16, W=32, C=3, V=4, light=0x1000, brdf=0x2000, params=0x6000, vis=0x3000, sv=512, out=0x4000,
+             work=0x5000)
+    a.update(args)
+    st = lib.lib().haar_shade_triple(a["H"], a["W"], a["C"], a["V"], a["light"], a["brdf"], a["params"], a["vis"],
+                                     a["sv"], a["out"], a["work"], None)
+    assert st == getattr(lib, "HAAR_ERR_" + err)
+    assert lib.lib().haar_shade_triple_work_floats(16, 32, 3) > 0

@@ -1,4 +1,4 @@
-"""The rotation kernel's atan2 (octant reduction + a degree-7 polynomial in
+"""The rotation kernels' atan2 (octant reduction + a degree-7 polynomial in
 t^2, coefficients fitted for that kernel) evaluated step by step in float32
 on the CPU against numpy's float64 atan2: the coordinate error it adds is
 bounded here, independently of the GPU."""
@@ -7,7 +7,7 @@ import re
 
 import numpy as np
 
-SRC = os.path.join(os.path.dirname(__file__), "..", "paper_1705_07272_gb300", "csrc", "shift.cu")
+SRC = os.path.join(os.path.dirname(__file__), "..", "paper_1705_07272_gb300", "csrc", "common.cuh")
 
 
 def _coeffs():
