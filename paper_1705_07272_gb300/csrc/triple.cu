@@ -204,11 +204,11 @@ __global__ void __launch_bounds__(kTripleThreads) k_triple(TripleArgs a) {
 // The rotation pass and the triple integral pass in one kernel, one CTA per
 // vertex.  The vertex's BRDF map is resampled under its rotation record
 // (g(w) = f(R w), bilinear, SPHERE extension: the exact operator of
-// haar_shift's rotations) straight into shared memory.  It is then
-// Haar-analysed bottom up, and each square's BRDF details and mean (its
-// scaling coefficient / B) enter the same case sum as k_triple, with the
-// visibility's details and top-down means.  The rotated BRDF never reaches
-// memory.
+// haar_shift's rotations), 2 x 2 pixels per thread, straight into the first
+// level of a bottom-up Haar analysis in shared memory.  Each square's BRDF
+// details and mean (its scaling value / B) enter the same case sum as
+// k_triple, with the visibility's details and top-down means.  Neither the
+// rotated BRDF nor its pixels reach memory.
 struct ShadeTripleArgs {
   TripleArgs t;
   const float* F;            // [H][W] the local BRDF map in pixels
@@ -261,14 +261,40 @@ __global__ void __launch_bounds__(256) k_shade_triple_setup(ShadeTripleArgs s, c
   }
 }
 
+// The rotated BRDF at output pixel (i, j): q = R p(theta_i, phi_j), source
+// position (Theta / dtheta - 1/2, Phi / dphi - 1/2), bilinear with the SPHERE
+// extension (one reflection across a pole at most: u in [-1/2, H - 1/2]).
+__device__ __forceinline__ float rot_sample(const ShadeTripleArgs& s, const float (&R)[9], int i, int j,
+                                            float inv_dth, float inv_dph) {
+  const TripleArgs& a = s.t;
+  const float2 th = s.tab_t[i], ph = s.tab_p[j];
+  const float p0 = th.x * ph.x, p1 = th.y, p2 = th.x * ph.y;
+  const float qx = R[0] * p0 + R[1] * p1 + R[2] * p2;
+  const float qy = R[3] * p0 + R[4] * p1 + R[5] * p2;
+  const float qz = R[6] * p0 + R[7] * p1 + R[8] * p2;
+  const float u = fmaf(rot_atan2(sqrtf(qx * qx + qz * qz), qy), inv_dth, -0.5f);
+  const float w = fmaf(rot_atan2(qx, qz), inv_dph, -0.5f);
+  const float fi = floorf(u), fj = floorf(w);
+  const float fu = u - fi, fv = w - fj;
+  const int i0 = (int)fi, j0 = (int)fj;
+  int r0 = i0, r1 = i0 + 1, s0 = 0, s1 = 0;
+  if (r0 < 0) { r0 = -1 - r0; s0 = a.W >> 1; }
+  if (r1 >= a.H) { r1 = 2 * a.H - 1 - r1; s1 = a.W >> 1; }
+  r0 = min(max(r0, 0), a.H - 1);                   // only a non-finite record gets clamped
+  r1 = min(max(r1, 0), a.H - 1);
+  const int m = a.W - 1;
+  const float f00 = __ldg(s.F + r0 * a.W + ((j0 + s0) & m)), f01 = __ldg(s.F + r0 * a.W + ((j0 + 1 + s0) & m));
+  const float f10 = __ldg(s.F + r1 * a.W + ((j0 + s1) & m)), f11 = __ldg(s.F + r1 * a.W + ((j0 + 1 + s1) & m));
+  return (1.0f - fu) * ((1.0f - fv) * f00 + fv * f01) + fu * ((1.0f - fv) * f10 + fv * f11);
+}
+
 template <int C, int T>
 __global__ void __launch_bounds__(T) k_shade_triple(ShadeTripleArgs s) {
   const TripleArgs& a = s.t;
   extern __shared__ __align__(16) float sm[];
-  float* G = sm;                       // [H][W] rotated BRDF pixels
-  float* sc = G + a.N;                 // [N] visibility row
+  float* sc = sm;                      // [N] visibility row
   float* mc = sc + a.N;                // [Nm] visibility means, level n first
-  float* sa = mc + a.Nm;               // [Nm] the BRDF's scaling values A_l, same layout
+  float* sa = mc + a.Nm;               // [Nm] the rotated BRDF's scaling values A_l, same layout
   __shared__ __align__(8) unsigned long long bar;
   __shared__ int abort_flag;
   __shared__ float red[T / 32][C];
@@ -284,35 +310,11 @@ __global__ void __launch_bounds__(T) k_shade_triple(ShadeTripleArgs s) {
     tc::mbar_arrive_tx(b32, (uint32_t)a.N * 4u);
     bulk_g2s(tc::smem_u32(sc), a.vis + (long long)v * a.sv, (uint32_t)a.N * 4u, b32);
   }
-  // rotation pass while the visibility row arrives
   float R[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) R[k] = (float)s.params[9 * (long long)v + k];
   const int logW = 31 - __clz(a.W);
   const float inv_dth = (float)a.H * 0.318309886183791f, inv_dph = (float)a.W * 0.159154943091895f;
-  for (int px = t; px < a.N; px += T) {
-    const int i = px >> logW, j = px & (a.W - 1);
-    const float2 th = s.tab_t[i], ph = s.tab_p[j];
-    const float p0 = th.x * ph.x, p1 = th.y, p2 = th.x * ph.y;
-    const float qx = R[0] * p0 + R[1] * p1 + R[2] * p2;
-    const float qy = R[3] * p0 + R[4] * p1 + R[5] * p2;
-    const float qz = R[6] * p0 + R[7] * p1 + R[8] * p2;
-    const float u = fmaf(rot_atan2(sqrtf(qx * qx + qz * qz), qy), inv_dth, -0.5f);
-    const float w = fmaf(rot_atan2(qx, qz), inv_dph, -0.5f);
-    const float fi = floorf(u), fj = floorf(w);
-    const float fu = u - fi, fv = w - fj;
-    int i0 = (int)fi, j0 = (int)fj;
-    // rows i0 and i0 + 1 with one reflection across a pole at most (u in [-1/2, H - 1/2])
-    int r0 = i0, r1 = i0 + 1, s0 = 0, s1 = 0;
-    if (r0 < 0) { r0 = -1 - r0; s0 = a.W >> 1; }
-    if (r1 >= a.H) { r1 = 2 * a.H - 1 - r1; s1 = a.W >> 1; }
-    r0 = min(max(r0, 0), a.H - 1);                   // only a non-finite record gets clamped
-    r1 = min(max(r1, 0), a.H - 1);
-    const int m = a.W - 1;
-    const float f00 = __ldg(s.F + r0 * a.W + ((j0 + s0) & m)), f01 = __ldg(s.F + r0 * a.W + ((j0 + 1 + s0) & m));
-    const float f10 = __ldg(s.F + r1 * a.W + ((j0 + s1) & m)), f11 = __ldg(s.F + r1 * a.W + ((j0 + 1 + s1) & m));
-    G[px] = (1.0f - fu) * ((1.0f - fv) * f00 + fv * f01) + fu * ((1.0f - fv) * f10 + fv * f11);
-  }
   bool ok = true;
   if (t < 32) ok = tc::mbar_wait(b32, 0, a.status, &abort_flag);
   if (!__syncthreads_and(ok)) {
@@ -331,18 +333,30 @@ __global__ void __launch_bounds__(T) k_shade_triple(ShadeTripleArgs s) {
                    sc[3 * g + k], invB);
     __syncthreads();
   }
-  // BRDF analysis bottom up, with the case sum of every square
+  // the rotated BRDF analysed bottom up, with the case sum of every square;
+  // level 1 resamples its 2 x 2 pixels itself (the pixels are never stored)
   float acc[C];
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
   for (int l = 1; l <= a.n; ++l) {
     const int g = a.q << (2 * (a.n - l)), cols = a.W >> l, lc = logW - l, moff = mean_off(g, a.q);
     const float invB = 1.0f / (float)(1 << l);
-    const float* src = (l == 1) ? G : sa + moff + g;   // A_{l-1}, [2 rows][2 cols]
+    const float* src = sa + moff + g;                 // A_{l-1}, [2 rows][2 cols] (l > 1)
     for (int k = t; k < g; k += T) {
       const int r = k >> lc, col = k & (cols - 1);
-      const float* c0 = src + (2 * r) * (2 * cols) + 2 * col;
-      const float ta = c0[0], tb = c0[1], tc_ = c0[2 * cols], td = c0[2 * cols + 1];
+      float ta, tb, tc_, td;
+      if (l == 1) {
+        ta = rot_sample(s, R, 2 * r, 2 * col, inv_dth, inv_dph);
+        tb = rot_sample(s, R, 2 * r, 2 * col + 1, inv_dth, inv_dph);
+        tc_ = rot_sample(s, R, 2 * r + 1, 2 * col, inv_dth, inv_dph);
+        td = rot_sample(s, R, 2 * r + 1, 2 * col + 1, inv_dth, inv_dph);
+      } else {
+        const float* c0 = src + (2 * r) * (2 * cols) + 2 * col;
+        ta = c0[0];
+        tb = c0[1];
+        tc_ = c0[2 * cols];
+        td = c0[2 * cols + 1];
+      }
       const float A = 0.5f * (ta + tb + tc_ + td);
       const float bH = 0.5f * (tb + td - ta - tc_), bV = 0.5f * (tc_ + td - ta - tb), bD = 0.5f * (ta + td - tb - tc_);
       const float mbk = A * invB;
@@ -400,7 +414,7 @@ static haar_status_t launch_shade_triple_c(const ShadeTripleArgs& s, const float
   k_shade_triple_setup<<<C + 1, 256, setup_smem, st>>>(s, brdf_local, F, tab_t, tab_p);
   haar_status_t r = cuda_check(cudaGetLastError(), "k_shade_triple_setup launch");
   if (r != HAAR_OK) return r;
-  const size_t smem = (2 * (size_t)a.N + 2 * (size_t)a.Nm) * sizeof(float);
+  const size_t smem = ((size_t)a.N + 2 * (size_t)a.Nm) * sizeof(float);
   if (a.N <= 2048) {
     e = cudaFuncSetAttribute(k_shade_triple<C, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "k_shade_triple attribute");
