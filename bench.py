@@ -476,6 +476,53 @@ def measure_rows(hs, dev, flush, only=None):
                                                "(haar_shade_triple), unfused = haar_shift + haar_triple_product",
                                        "levels": levels}
 
+    # the paper's whole frame with a headless rasteriser in place of its Cg pass
+    # (N4): a 50 176-vertex torus mesh shaded per vertex by the fused shading
+    # loop (level 5, Lambertian, c1 occluders), rasterised at 1920x1080
+    # (triangle id + perspective-correct barycentrics per pixel) and shaded
+    # per pixel by interpolating the vertex radiance
+    if want("raster_frame"):
+        sc1 = synth.scene(1, V=1)
+        pos_np, nrm_np, tris_np = synth.torus_mesh(256, 196)
+        V, T = len(pos_np), len(tris_np)
+        H, W = 32, 64
+        Wi, Hi = 1920, 1080
+        pos = torch.tensor(pos_np, device=dev)
+        nrm = torch.tensor(nrm_np, device=dev)
+        tris = torch.tensor(tris_np, device=dev)
+        M = torch.tensor(synth.view_projection((0.4, 1.6, 2.6), (0.0, 0.0, 0.0), aspect=Wi / Hi).reshape(-1),
+                         device=dev)
+        light = hs.haar_forward(torch.tensor(synth.lighting_pixels(synth.rng_for(1, 45), 3, H, W),
+                                             dtype=torch.float32, device=dev))
+        brdf = hs.haar_forward(torch.tensor(synth.local_brdf_map(H, W), dtype=torch.float32, device=dev)[None])[0]
+        w = synth.transport_weights(pos_np, nrm_np, sc1["occ_c"], sc1["occ_r"], H, W, device=dev,
+                                    dtype=torch.float32, chunk=4096, cosine=False).contiguous()
+        vis = hs.haar_forward(w)
+        del w
+        prm = torch.empty((V, 9), dtype=torch.float64, device=dev)
+        rad = torch.empty((V, 3), dtype=torch.float32, device=dev)
+        work = torch.empty(hs.haar_shade_triple_work_floats(H, W, 3), dtype=torch.float32, device=dev)
+        rs = hs.Raster(Wi, Hi, V)
+        bg = torch.zeros(3, dtype=torch.float32, device=dev)
+        img = torch.empty((Hi, Wi, 3), dtype=torch.float32, device=dev)
+
+        def frame():
+            hs.haar_normal_rotations(nrm, prm)
+            hs.haar_shade_triple(H, W, light, brdf, prm, vis, rad, work)
+            rs.rasterize(pos, tris, M)
+            rs.shade(tris, rad, bg, img)
+
+        frame()
+        covered = int((rs.tri_id >= 0).sum().item())
+        ms_frame = _timeit(frame, 10, flush, stream)
+        ms_raster = _timeit(lambda: rs.rasterize(pos, tris, M), 10, flush, stream)
+        ms_pix = _timeit(lambda: rs.shade(tris, rad, bg, img), 10, flush, stream)
+        rows["raster_frame"] = {"what": "torus mesh of 50 176 vertices / 100 352 triangles: fused per-vertex "
+                                        "shading loop (32x64, RGB) + headless rasterisation at 1920x1080 + "
+                                        "per-pixel interpolation", "frame_ms": ms_frame,
+                                "frames_per_s": 1e3 / ms_frame, "raster_ms": ms_raster, "pixel_shade_ms": ms_pix,
+                                "covered_pixels": covered, "triangles": T, "vertices": V}
+
     # c2 frame: 64 rotations -> bf16 hi/lo lowest 4096 -> tcgen05 contraction for 200k vertices
     if want("c2_dense_tc"):
         sc2 = synth.scene(2)

@@ -326,6 +326,42 @@ HAAR_API haar_status_t haar_shade_triple(int H, int W, int C, int V, const float
                                          float* work, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Headless rasterisation (the paper's rasterisation pass, Sec. "Experimental
+ * results", without a graphics API): a fragment buffer of the nearest
+ * triangle and its perspective-correct barycentrics per pixel, then per-pixel
+ * shading from per-vertex radiance.
+ * ------------------------------------------------------------------------- */
+
+/* pos: [V][3] float32; tris: [T][3] int32 vertex indices (a triangle with an
+ * index outside [0, V) is dropped); view_proj: 16 float32, row-major,
+ * device.  Each vertex is projected as clip = M [x y z 1], ndc = clip / w,
+ * screen = ((ndc_x + 1) / 2 width, (1 - ndc_y) / 2 height), rows growing
+ * downwards.  A triangle with a vertex at w <= 1e-6 is dropped (no near-plane
+ * clipping).  Pixel (px, py) samples its centre (px + 1/2, py + 1/2).  It is
+ * covered when the edge functions, oriented to a positive screen area, are
+ * > 0, or = 0 on an edge whose direction has dy > 0, or dy = 0 and dx < 0.
+ * That rule covers an edge shared by two triangles once.  Depth = (ndc z
+ * interpolated + 1) / 2 must lie in [0, 1]; the nearest fragment wins, and on
+ * equal depth the lower triangle id.  These decisions are float32 with a
+ * fixed operation order and no fused multiply-add.
+ * Outputs, for an image of width x height pixels (row-major):
+ *   tri_id [H][W] int32, -1 where nothing is hit;
+ *   bary [H][W][2] float32, the weights of the triangle's vertices 1 and 2
+ *     (vertex 0 gets 1 - b1 - b2), perspective-correct;
+ *   screen [V][4] float32 (16-byte aligned) and zbuf [H][W] uint64 are
+ *     scratch (zbuf: depth bits << 32 | triangle id). */
+HAAR_API haar_status_t haar_rasterize(int V, const float* pos, int T, const int32_t* tris, const float* view_proj,
+                                      int width, int height, float* screen, unsigned long long* zbuf,
+                                      int32_t* tri_id, float* bary, void* stream);
+
+/* image [H][W][C] float32 = the barycentric interpolation of vert_rad [V][C]
+ * over each pixel's triangle (from haar_rasterize), background [C] where
+ * tri_id is -1 or not a valid triangle of tris [T][3]. */
+HAAR_API haar_status_t haar_shade_pixels(int width, int height, int C, int V, int T, const int32_t* tri_id,
+                                         const float* bary, const int32_t* tris, const float* vert_rad,
+                                         const float* background, float* image, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Transport surrogate (not in the paper; a learned stand-in for stored
  * transport).  A 4 x 256 GELU MLP (tanh-form GELU) maps a vertex's position, normal and view
  * direction to its transport coefficients at a fixed set of 512 canonical

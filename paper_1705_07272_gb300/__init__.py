@@ -54,7 +54,8 @@ EXPORTS = ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_for
            "haar_mlp_destroy", "haar_mlp_set_params", "haar_mlp_get_params", "haar_mlp_forward",
            "haar_mlp_grads", "haar_mlp_train_step", "haar_mlp_shade", "haar_mlp_status",
            "haar_shift_noalloc", "haar_transport_group", "haar_shift_plan_status", "haar_normal_rotations",
-           "haar_triple_work_floats", "haar_triple_product", "haar_shade_triple_work_floats", "haar_shade_triple")
+           "haar_triple_work_floats", "haar_triple_product", "haar_shade_triple_work_floats", "haar_shade_triple",
+           "haar_rasterize", "haar_shade_pixels")
 
 
 class HaarShiftDesc(ctypes.Structure):
@@ -111,6 +112,10 @@ def lib() -> ctypes.CDLL:
     L.haar_shade_triple_work_floats.restype = ctypes.c_longlong
     L.haar_shade_triple.argtypes = [i, i, i, i, vp, vp, vp, vp, ctypes.c_longlong, vp, vp, vp]
     L.haar_shade_triple.restype = st
+    L.haar_rasterize.argtypes = [i, vp, i, vp, vp, i, i, vp, vp, vp, vp, vp]
+    L.haar_rasterize.restype = st
+    L.haar_shade_pixels.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp, vp, vp]
+    L.haar_shade_pixels.restype = st
     for name in ("haar_shift_plan", "haar_shift_plan_destroy", "haar_shift", "haar_shift_noalloc", "haar_forward", "haar_inverse",
                  "shade_vertices", "shade_batch", "haar_view_bins"):
         getattr(L, name).restype = st
@@ -404,6 +409,43 @@ def haar_shade_triple(H, W, light, brdf_local, params, vis, out=None, work=None,
                                    vis.data_ptr(), vis.stride(0), _dev(out, torch.float32, "out"),
                                    _dev(work, torch.float32, "work"), _stream(stream)))
     return out
+
+
+class Raster:
+    """Device buffers of a headless rasteriser for a width x height image and
+    V vertices; rasterize() fills tri_id [H][W] and bary [H][W][2]."""
+
+    def __init__(self, width, height, V, device="cuda"):
+        import torch
+        self.width, self.height, self.V = width, height, V
+        self.screen = torch.empty((max(V, 1), 4), dtype=torch.float32, device=device)
+        self.zbuf = torch.empty((height, width), dtype=torch.int64, device=device)
+        self.tri_id = torch.empty((height, width), dtype=torch.int32, device=device)
+        self.bary = torch.empty((height, width, 2), dtype=torch.float32, device=device)
+
+    def rasterize(self, pos, tris, view_proj, stream=None):
+        import torch
+        V, T = pos.shape[0], tris.shape[0]
+        if V > self.V:
+            raise ValueError(f"{V} vertices > {self.V}")
+        _check(lib().haar_rasterize(V, _dev(pos, torch.float32, "pos"), T, _dev(tris, torch.int32, "tris"),
+                                    _dev(view_proj, torch.float32, "view_proj"), self.width, self.height,
+                                    self.screen.data_ptr(), self.zbuf.data_ptr(), self.tri_id.data_ptr(),
+                                    self.bary.data_ptr(), _stream(stream)))
+        return self.tri_id, self.bary
+
+    def shade(self, tris, vert_rad, background, image=None, stream=None):
+        """image [H][W][C]: per-vertex radiance [V][C] interpolated per pixel."""
+        import torch
+        C = vert_rad.shape[1]
+        if image is None:
+            image = torch.empty((self.height, self.width, C), dtype=torch.float32, device=vert_rad.device)
+        _check(lib().haar_shade_pixels(self.width, self.height, C, vert_rad.shape[0], tris.shape[0],
+                                       self.tri_id.data_ptr(), self.bary.data_ptr(), _dev(tris, torch.int32, "tris"),
+                                       _dev(vert_rad, torch.float32, "vert_rad"),
+                                       _dev(background, torch.float32, "background"),
+                                       _dev(image, torch.float32, "image"), _stream(stream)))
+        return image
 
 
 class Surrogate:

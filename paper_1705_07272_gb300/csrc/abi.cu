@@ -394,4 +394,34 @@ haar_status_t haar_shade_triple(int H, int W, int C, int V, const float* light, 
                              (cudaStream_t)stream);
 }
 
+haar_status_t haar_rasterize(int V, const float* pos, int T, const int32_t* tris, const float* view_proj, int width,
+                             int height, float* screen, unsigned long long* zbuf, int32_t* tri_id, float* bary,
+                             void* stream) {
+  HS_ENTRY("haar_rasterize");
+  if (V < 0 || T < 0 || width < 1 || height < 1 || width > 16384 || height > 16384)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_rasterize: V=%d T=%d image %d x %d", V, T, width, height);
+  if ((V > 0 && (!pos || !screen)) || (T > 0 && !tris) || !view_proj || !zbuf || !tri_id || !bary)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_rasterize: null pointer");
+  if (!aligned(pos, 4) || !aligned(tris, 4) || !aligned(view_proj, 4) || !aligned(screen, 16) || !aligned(zbuf, 8) ||
+      !aligned(tri_id, 4) || !aligned(bary, 8))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_rasterize: misaligned pointer");
+  return launch_rasterize(V, pos, T, tris, view_proj, width, height, screen, zbuf, tri_id, bary,
+                          (cudaStream_t)stream);
+}
+
+haar_status_t haar_shade_pixels(int width, int height, int C, int V, int T, const int32_t* tri_id, const float* bary,
+                                const int32_t* tris, const float* vert_rad, const float* background, float* image,
+                                void* stream) {
+  HS_ENTRY("haar_shade_pixels");
+  if (width < 1 || height < 1 || width > 16384 || height > 16384 || C < 1 || C > 64 || V < 0 || T < 0)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_pixels: image %d x %d C=%d V=%d T=%d", width, height, C, V, T);
+  if (!tri_id || !bary || (T > 0 && !tris) || (V > 0 && !vert_rad) || !background || !image)
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_pixels: null pointer");
+  if (!aligned(bary, 8) || !aligned(tri_id, 4) || !aligned(tris, 4) || !aligned(vert_rad, 4) ||
+      !aligned(background, 4) || !aligned(image, 4))
+    return set_error(HAAR_ERR_INVALID_ARG, "haar_shade_pixels: misaligned pointer");
+  return launch_shade_pixels(width, height, C, V, T, tri_id, bary, tris, vert_rad, background, image,
+                             (cudaStream_t)stream);
+}
+
 }  // extern "C"

@@ -184,6 +184,12 @@ haar_status_t launch_triple(int H, int W, int C, int V, const float* light, cons
                             const float* vis, long long sv, float* out, float* work, cudaStream_t st);
 long long triple_work_floats(int H, int W, int C);
 long long shade_triple_work_floats(int H, int W, int C);
+haar_status_t launch_rasterize(int V, const float* pos, int T, const int32_t* tris, const float* M, int width,
+                               int height, float* screen, unsigned long long* zbuf, int32_t* tri_id, float* bary,
+                               cudaStream_t st);                                     // raster.cu
+haar_status_t launch_shade_pixels(int width, int height, int C, int V, int T, const int32_t* tri_id,
+                                  const float* bary, const int32_t* tris, const float* rad, const float* bg,
+                                  float* img, cudaStream_t st);
 haar_status_t launch_shade_triple(int H, int W, int C, int V, const float* light, const float* brdf_local,
                                   const double* params, const float* vis, long long sv, float* out, float* work,
                                   cudaStream_t st);

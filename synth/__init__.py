@@ -114,6 +114,44 @@ def local_brdf_map(H: int, W: int, expo: float = 0.0, view_theta: float = 0.0) -
     return (expo + 2.0) / (2.0 * math.pi) * np.maximum(d @ r, 0.0) ** expo * cos
 
 
+def torus_mesh(nu: int, nv: int, R: float = 1.0, r: float = 0.4):
+    """A closed triangle mesh of the torus (axis Y, core radius R, tube radius
+    r) on an nu x nv parameter grid: positions and normals [nu nv, 3] float32,
+    triangles [2 nu nv, 3] int32, consistently wound."""
+    u = np.arange(nu) * 2.0 * math.pi / nu
+    v = np.arange(nv) * 2.0 * math.pi / nv
+    U, Vv = np.meshgrid(u, v, indexing="ij")
+    ring = R + r * np.cos(Vv)
+    pos = np.stack([ring * np.sin(U), r * np.sin(Vv), ring * np.cos(U)], -1).reshape(-1, 3)
+    nrm = np.stack([np.cos(Vv) * np.sin(U), np.sin(Vv), np.cos(Vv) * np.cos(U)], -1).reshape(-1, 3)
+    i, j = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    a = i * nv + j
+    b = ((i + 1) % nu) * nv + j
+    c = ((i + 1) % nu) * nv + (j + 1) % nv
+    d = i * nv + (j + 1) % nv
+    tris = np.concatenate([np.stack([a, b, c], -1).reshape(-1, 3), np.stack([a, c, d], -1).reshape(-1, 3)])
+    return pos.astype(np.float32), nrm.astype(np.float32), tris.astype(np.int32)
+
+
+def view_projection(eye, target, up=(0.0, 1.0, 0.0), fov_y: float = 0.8, aspect: float = 16 / 9,
+                    near: float = 0.1, far: float = 20.0) -> np.ndarray:
+    """Row-major 4 x 4 float32 perspective x look-at matrix (OpenGL clip
+    conventions: the camera looks down -z of its frame, ndc z in [-1, 1])."""
+    eye, target, up = (np.asarray(x, dtype=np.float64) for x in (eye, target, up))
+    f = target - eye
+    f /= np.linalg.norm(f)
+    s_ = np.cross(f, up)
+    s_ /= np.linalg.norm(s_)
+    u_ = np.cross(s_, f)
+    view = np.eye(4)
+    view[0, :3], view[1, :3], view[2, :3] = s_, u_, -f
+    view[:3, 3] = -view[:3, :3] @ eye
+    t = 1.0 / math.tan(fov_y / 2)
+    proj = np.array([[t / aspect, 0, 0, 0], [0, t, 0, 0],
+                     [0, 0, (far + near) / (near - far), 2 * far * near / (near - far)], [0, 0, -1, 0]])
+    return (proj @ view).astype(np.float32)
+
+
 def sphere_vertices(rng: np.random.Generator, V: int):
     """Vertices uniform on the unit sphere; normal = position."""
     p = uniform_sphere(rng, V)

@@ -156,3 +156,19 @@ def test_shade_triple_rejects_bad_arguments(lib, args, err):
                                      a["sv"], a["out"], a["work"], None)
     assert st == getattr(lib, "HAAR_ERR_" + err)
     assert lib.lib().haar_shade_triple_work_floats(16, 32, 3) > 0
+
+
+def test_raster_rejects_bad_arguments(lib):
+    L = lib.lib()
+    ok = dict(V=3, pos=0x1000, T=1, tris=0x2000, M=0x3000, w=16, h=16, screen=0x4000, zbuf=0x5000, tid=0x6000,
+              bary=0x7000)
+    for bad in (dict(w=0), dict(h=20000), dict(V=-1), dict(T=-2), dict(pos=0), dict(M=0), dict(screen=0x4008),
+                dict(zbuf=0x5004), dict(bary=0x7004)):
+        a = dict(ok, **bad)
+        st = L.haar_rasterize(a["V"], a["pos"], a["T"], a["tris"], a["M"], a["w"], a["h"], a["screen"], a["zbuf"],
+                              a["tid"], a["bary"], None)
+        assert st == lib.HAAR_ERR_INVALID_ARG, bad
+    assert L.haar_shade_pixels(16, 16, 0, 3, 1, 0x1000, 0x2000, 0x3000, 0x4000, 0x5000, 0x6000, None) == \
+        lib.HAAR_ERR_INVALID_ARG
+    assert L.haar_shade_pixels(16, 16, 3, 3, 1, 0x1000, 0x2004, 0x3000, 0x4000, 0x5000, 0x6000, None) == \
+        lib.HAAR_ERR_INVALID_ARG
