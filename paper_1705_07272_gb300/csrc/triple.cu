@@ -104,8 +104,6 @@ __global__ void __launch_bounds__(256) k_triple_means(TripleArgs a, float* ma, f
   light_means(a, blockIdx.x, ma, pk);
 }
 
-constexpr int kTripleThreads = 128;
-
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
@@ -115,8 +113,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 // One CTA per vertex: both factors' rows arrive in shared memory by two bulk
 // copies, then the squares are visited level by level from the coarsest, the
 // factors' means for the next level written as they go.
-template <int C>
-__global__ void __launch_bounds__(kTripleThreads) k_triple(TripleArgs a) {
+template <int C, int T>
+__global__ void __launch_bounds__(T) k_triple(TripleArgs a) {
   extern __shared__ __align__(16) float sm[];
   float* sb = sm;                      // [N] BRDF row
   float* sc = sm + a.N;                // [N] visibility row
@@ -124,7 +122,7 @@ __global__ void __launch_bounds__(kTripleThreads) k_triple(TripleArgs a) {
   float* mc = mb + a.Nm;               // [Nm] visibility means
   __shared__ __align__(8) unsigned long long bar;
   __shared__ int abort_flag;
-  __shared__ float red[kTripleThreads / 32][C];
+  __shared__ float red[T / 32][C];
   const int v = blockIdx.x, t = threadIdx.x;
   const uint32_t b32 = tc::smem_u32(&bar);
   if (t == 0) {
@@ -149,7 +147,7 @@ __global__ void __launch_bounds__(kTripleThreads) k_triple(TripleArgs a) {
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
   const float invH = 1.0f / (float)a.H;
-  for (int k = t; k < a.q; k += kTripleThreads) {          // three scaling functions
+  for (int k = t; k < a.q; k += T) {          // three scaling functions
     const float bc = sb[k] * sc[k];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) acc[ch] += __ldg(a.light + (long long)ch * a.N + k) * bc * invH;
@@ -161,7 +159,7 @@ __global__ void __launch_bounds__(kTripleThreads) k_triple(TripleArgs a) {
   for (int l = a.n; l >= 1; --l) {
     const int g = a.q << (2 * (a.n - l)), cols = a.W >> l, lc = logW - l, moff = mean_off(g, a.q);
     const float invB = 1.0f / (float)(1 << l);
-    for (int k = t; k < g; k += kTripleThreads) {
+    for (int k = t; k < g; k += T) {
       const float bH = sb[g + k], bV = sb[2 * g + k], bD = sb[3 * g + k];
       const float cH = sc[g + k], cV = sc[2 * g + k], cD = sc[3 * g + k];
       const float mbk = mb[moff + k], mck = mc[moff + k];
@@ -194,7 +192,7 @@ __global__ void __launch_bounds__(kTripleThreads) k_triple(TripleArgs a) {
   if (t < C) {
     float x = 0.0f;
 #pragma unroll
-    for (int w = 0; w < kTripleThreads / 32; ++w) x += red[w][t];
+    for (int w = 0; w < T / 32; ++w) x += red[w][t];
     a.out[(long long)v * C + t] = x;
   }
 }
@@ -484,12 +482,14 @@ size_t triple_smem_bytes(int H, int W) {
 template <int C>
 static haar_status_t launch_triple_c(const TripleArgs& a, float* ma, cudaStream_t st) {
   const size_t smem = triple_smem_bytes(a.H, a.W);
-  cudaError_t e = cudaFuncSetAttribute(k_triple<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_check(e, "k_triple attribute");
   k_triple_means<<<C, 256, 0, st>>>(a, ma, const_cast<float4*>(a.pk));
   haar_status_t r = cuda_check(cudaGetLastError(), "k_triple_means launch");
   if (r != HAAR_OK) return r;
-  k_triple<C><<<a.V, kTripleThreads, smem, st>>>(a);
+  // 128 threads at every size: at 64 x 128 shared memory allows 2 CTAs per
+  // SM, and 256 threads per CTA measured slower (1.62 against 1.37 ms)
+  cudaError_t e = cudaFuncSetAttribute(k_triple<C, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_check(e, "k_triple attribute");
+  k_triple<C, 128><<<a.V, 128, smem, st>>>(a);
   return cuda_check(cudaGetLastError(), "k_triple launch");
 }
 
