@@ -205,6 +205,17 @@ def test_csr_full_size_c1_sampled(hs):
     Rg = hs.shade_batch(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), trg).cpu().numpy()
     assert rel_l2(Rg[pick], ref) <= 1e-5
     assert rel_l2(Rg, got) <= 1e-6
+    # shaded in vertex chunks (group-aligned slices of the group offsets, as the
+    # end-to-end bench streams results back): the same bits as one launch
+    lit = torch.empty((H * W, sc["S"], 3), dtype=torch.float32, device="cuda")
+    hs.haar_shift(plan, _t(L, torch.float32), _t(sc["params"], torch.float64), lit)
+    whole = hs.shade_vertices(plan, trg, lit, sc["S"])
+    parts = torch.empty_like(whole)
+    bounds = [0, 12500, 24996, 37500, sc["V"]]
+    for v0, v1 in zip(bounds[:-1], bounds[1:]):
+        trk = hs.Transport(hs.HAAR_T_GCSR_F32_U16, v1 - v0, 0, trg.vals, trg.idx, trg.rowptr[v0 // hs.GROUP:])
+        hs.shade_vertices(plan, trk, lit, sc["S"], parts[v0:v1])
+    assert torch.equal(parts, whole)
 
 
 def test_view_bins(hs):
