@@ -282,7 +282,6 @@ struct ChSpec {
   float w;
 };
 __device__ __forceinline__ ChSpec ch_minus_half(float f) { return f >= 0.5f ? ChSpec{1, f - 0.5f} : ChSpec{0, f + 0.5f}; }
-__device__ __forceinline__ ChSpec ch_plus_half(float f) { return f >= 0.5f ? ChSpec{2, f - 0.5f} : ChSpec{1, f + 0.5f}; }
 
 // floor of the position iu + fu and its fraction
 __device__ __forceinline__ void ch_split(int ib, float fb, int& i0, float& fr) {
@@ -382,60 +381,64 @@ __global__ void __launch_bounds__(256, 2) k_chain_tile(ChainArgs a) {
       ch_load<2, 2>(F, o0, T);
       gv = ch_lerp(ch_lerp(T[0][0], T[0][1], f0v), ch_lerp(T[1][0], T[1][1], f0v), f0u);
     }
-    // g_theta at (i + 1/2, j) and g_phi at (i, j + 1/2): the centred first
-    // differences F(u +- 1/2, v) and F(u, v +- 1/2) on a 3 x 3 window whose
-    // origin is floor(u + 1/2) - 1 (fraction e); the samples at the position
-    // itself sit at e -+ 1/2 from rows 0 / 1
+    // The source derivatives are differences of bilinear samples.  Since
+    // bilinear sampling is linear, each one is taken as the same interpolation
+    // of the taps' own differences (rows: dR[k] = T[k + 1] - T[k]; columns
+    // likewise).  On a smooth map neighbouring taps are close, so these
+    // differences are exact in float32, and the cancellation that differencing
+    // interpolated values would leave (amplified near a pole by the 1 / rho
+    // Jacobian factors) never happens.
+    //
+    // g_theta at (i + 1/2, j) and g_phi at (i, j + 1/2): F(u +- 1/2, v) and
+    // F(u, v +- 1/2) on a 3 x 3 window whose origin is floor(u + 1/2) - 1
+    // (fraction e); the position itself sits at e + 1/2 from row / column 0.
     auto first = [&](const int (&o)[3][3], float eu, float ev, const ChJac& J, bool theta) {
       float T[3][3];
       ch_load<3, 3>(F, o, T);
       const int ku = eu >= 0.5f ? 1 : 0, kv = ev >= 0.5f ? 1 : 0;
       const float wu = eu >= 0.5f ? eu - 0.5f : eu + 0.5f, wv = ev >= 0.5f ? ev - 0.5f : ev + 0.5f;
-      float rm[3], rp[3], r0_[3];
+      float du[3], dv[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        rm[c] = ch_lerp(T[0][c], T[1][c], eu);                 // row u - 1/2
-        rp[c] = ch_lerp(T[1][c], T[2][c], eu);                 // row u + 1/2
-        const float col[3] = {T[0][c], T[1][c], T[2][c]};
-        r0_[c] = ch_pick_lerp<3>(col, ku, wu);                 // row u
-      }
-      const float fu = ch_pick_lerp<3>(rp, kv, wv) - ch_pick_lerp<3>(rm, kv, wv);
-      const float fv = ch_lerp(r0_[1], r0_[2], ev) - ch_lerp(r0_[0], r0_[1], ev);
+      for (int c = 0; c < 3; ++c) du[c] = ch_lerp(T[1][c] - T[0][c], T[2][c] - T[1][c], eu);   // column c
+#pragma unroll
+      for (int r = 0; r < 3; ++r) dv[r] = ch_lerp(T[r][1] - T[r][0], T[r][2] - T[r][1], ev);   // row r
+      const float fu = ch_pick_lerp<3>(du, kv, wv);
+      const float fv = ch_pick_lerp<3>(dv, ku, wu);
       return theta ? fu * J.ui + fv * J.vi : fu * J.uj + fv * J.vj;
     };
     gt = first(oa, eau, eav, Ja, true);
     gp = first(ob, ebu, ebv, Jb, false);
-    {  // g_thetaphi at (i + 1/2, j + 1/2): second-order chain rule on a 4 x 4 window
+    {  // g_thetaphi at (i + 1/2, j + 1/2): second-order chain rule on a 4 x 4
+       // window with origin floor(u) - 1, so u sits at fcu from row 1
       float T[4][4];
       ch_load<4, 4>(F, oc, T);
-      const ChSpec um = ch_minus_half(fcu), up = ch_plus_half(fcu);
-      const ChSpec vm = ch_minus_half(fcv), vp = ch_plus_half(fcv);
-      float A[5][4];                                 // rows at u - 1, u - 1/2, u, u + 1/2, u + 1
+      const ChSpec um = ch_minus_half(fcu), vm = ch_minus_half(fcv);
+      float R[3][4], Cd[4][3];                        // row and column differences of the taps
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) R[k][c] = T[k + 1][c] - T[k][c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) Cd[r][l] = T[r][l + 1] - T[r][l];
+      // F(u + 1/2) - F(u - 1/2) at every column, F(v + 1/2) - F(v - 1/2) at every row
+      float dU[4], dV[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const float col[4] = {T[0][c], T[1][c], T[2][c], T[3][c]};
-        A[0][c] = ch_lerp(col[0], col[1], fcu);
-        A[1][c] = ch_pick_lerp<4>(col, um.k, um.w);
-        A[2][c] = ch_lerp(col[1], col[2], fcu);
-        A[3][c] = ch_pick_lerp<4>(col, up.k, up.w);
-        A[4][c] = ch_lerp(col[2], col[3], fcu);
+        const float col[3] = {R[0][c], R[1][c], R[2][c]};
+        dU[c] = ch_pick_lerp<3>(col, um.k, um.w);
       }
-      auto S = [&](int ar, int b) {                  // sample at row offset ar, column offset b (half units + 2)
-        const float(&R)[4] = A[ar];
-        switch (b) {
-          case 0: return ch_lerp(R[0], R[1], fcv);
-          case 1: return ch_pick_lerp<4>(R, vm.k, vm.w);
-          case 2: return ch_lerp(R[1], R[2], fcv);
-          case 3: return ch_pick_lerp<4>(R, vp.k, vp.w);
-          default: return ch_lerp(R[2], R[3], fcv);
-        }
-      };
-      const float f00 = S(2, 2);
-      const float fuu = S(4, 2) - 2.0f * f00 + S(0, 2);
-      const float fvv = S(2, 4) - 2.0f * f00 + S(2, 0);
-      const float fuv = S(3, 3) - S(3, 1) - S(1, 3) + S(1, 1);
-      const float fu = S(3, 2) - S(1, 2);
-      const float fv = S(2, 3) - S(2, 1);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) dV[r] = ch_pick_lerp<3>(Cd[r], vm.k, vm.w);
+      const float fu = ch_lerp(dU[1], dU[2], fcv);
+      const float fv = ch_lerp(dV[1], dV[2], fcu);
+      const float dUc[3] = {dU[1] - dU[0], dU[2] - dU[1], dU[3] - dU[2]};
+      const float fuv = ch_pick_lerp<3>(dUc, vm.k, vm.w);
+      const float fuu = ch_lerp(ch_lerp(R[1][1] - R[0][1], R[2][1] - R[1][1], fcu),
+                                ch_lerp(R[1][2] - R[0][2], R[2][2] - R[1][2], fcu), fcv);
+      const float fvv = ch_lerp(ch_lerp(Cd[1][1] - Cd[1][0], Cd[1][2] - Cd[1][1], fcv),
+                                ch_lerp(Cd[2][1] - Cd[2][0], Cd[2][2] - Cd[2][1], fcv), fcu);
       gtp = fuu * Jc.ui * Jc.uj + fuv * (Jc.ui * Jc.vj + Jc.uj * Jc.vi) + fvv * Jc.vi * Jc.vj + fu * Jc.uij +
             fv * Jc.vij;
     }

@@ -102,3 +102,27 @@ def test_fp32_coordinates_without_refinement_exceed_it(monkeypatch):
     # deviation is ~1e-4 (9.3e-5 here, 2.2e-4 at 128 x 256)
     err = _deviation(monkeypatch, refine=False)
     assert err.max() > 1e-5, err
+
+
+def test_float32_pixel_map_sets_the_floor_on_smooth_maps():
+    # The route differentiates the synthesised pixel map twice, and near a
+    # pole the mixed term multiplies those differences by v_theta v_phi ~
+    # 1 / rho^2.  On a band-limited map the second differences are ~1e-5 of
+    # the values, so rounding the map to float32 (half an ulp, as the GPU
+    # stores it) moves the result by ~1e-5..1e-4 when a rotation passes
+    # within 0.01 rad of a pole (here rotation 0 of the c2 set, rho = 7.7e-3).
+    # The GPU's synthesis carries a few ulp, so its bound on band-limited
+    # maps is 3e-4; on the per-pixel lognormal maps the same rounding is
+    # negligible and the bound stays 1e-5.
+    H, W = 64, 128
+    sc = synth.scene(2, V=1)
+    light = synth.smooth_lighting(np.random.default_rng(3), 3, H, W)
+    P = oh.inverse(f32(oh.forward(light)), H, W)[0]
+    R = resample.euler_matrix(*sc["params"][0])
+    ref = chain_rule.rotate_coeffs(P, R, 0)
+    got = chain_rule.rotate_coeffs(P.astype(np.float32).astype(np.float64), R, 0)
+    assert 1e-5 < rel_l2(got, ref) < 1e-4
+    # the lognormal map of the same size: the rounding stays below 1e-6
+    Pl = oh.inverse(f32(oh.forward(synth.lighting_pixels(np.random.default_rng(3), 1, H, W))), H, W)[0]
+    refl = chain_rule.rotate_coeffs(Pl, R, 0)
+    assert rel_l2(chain_rule.rotate_coeffs(Pl.astype(np.float32).astype(np.float64), R, 0), refl) < 1e-6

@@ -84,3 +84,23 @@ def test_pole_on_a_difference_midpoint(hs):
     ref = _oracle(c, H, W, eul)
     assert np.isfinite(got).all()
     assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
+
+
+@pytest.mark.parametrize("smooth", [True, False])
+def test_full_size_sampled(hs, smooth):
+    # the bench's launch: 64 rotations of RGB 256x512; the oracle checks two
+    # (rotation, channel) planes in full
+    H, W = 256, 512
+    sc = synth.scene(2, V=1)
+    light = synth.smooth_lighting(np.random.default_rng(3), 3, H, W) if smooth else sc["light"]
+    c = f32(oh.forward(light))
+    eul = np.asarray(sc["params"], dtype=np.float64)
+    got = _run(hs, c, H, W, eul)
+    assert got.shape == (64, 3, H * W) and np.isfinite(got).all()
+    P = oh.inverse(c, H, W)
+    # band-limited maps: the float32 pixel map sets the floor near a pole
+    # (tests/test_chain_fp32_budget.py); per-pixel noise: the FP32 bar
+    tol = 3e-4 if smooth else 1e-5
+    for s, ch in ((0, 0), (37, 2)):
+        ref = chain_rule.rotate_coeffs(P[ch], resample.euler_matrix(*eul[s]), 0)
+        assert rel_l2(got[s, ch], ref) <= tol, (s, ch, rel_l2(got[s, ch], ref))

@@ -69,3 +69,16 @@ def test_dropped_triangles(hs):
     assert (tid == -1).all()
     _, tid, _ = _run(hs, pos, np.zeros((0, 3), np.int32), M, 16, 16)
     assert (tid == -1).all()
+
+
+def test_full_size_frame_matches_the_oracle(hs):
+    # the bench's frame: the 50 176-vertex / 100 352-triangle torus at 1920x1080
+    W, H = 1920, 1080
+    pos, nrm, tris = synth.torus_mesh(256, 196)
+    M = synth.view_projection((0.4, 1.6, 2.6), (0.0, 0.0, 0.0), aspect=W / H)
+    _, tid, bary = _run(hs, pos, tris, M, W, H)
+    ref_tid, ref_bary, _ = ora.rasterize(pos, tris, M, W, H)
+    assert np.array_equal(tid, ref_tid)
+    hit = tid >= 0
+    assert hit.sum() > 500_000
+    assert np.abs(bary[hit] - ref_bary[hit]).max() <= 1e-4

@@ -142,3 +142,28 @@ def test_fused_shading_loop_matches_the_oracle(hs, H, W, C, expo):
     unfused = hs.haar_triple_product(H, W, lt, rot[:, 0, :], vt).cpu().numpy()
     plan.close()
     assert np.linalg.norm(got - unfused) / np.linalg.norm(unfused) <= 2e-5
+
+
+def test_full_size_fused_loop_sampled(hs):
+    # the bench's level-6 launch: 50 000 c1 torus vertices, RGB 64x128; the
+    # oracle shades 12 sampled vertices one by one
+    import torch
+    H, W = 64, 128
+    sc = synth.scene(1)
+    V = sc["V"]
+    dev = dict(dtype=torch.float32, device="cuda")
+    light = f32(oh.forward(synth.lighting_pixels(np.random.default_rng(46), 3, H, W)))
+    brdf = f32(oh.forward(synth.local_brdf_map(H, W)))
+    vis = torch.empty((V, H * W), **dev)
+    for v0 in range(0, V, 8192):
+        v1 = min(V, v0 + 8192)
+        w = synth.transport_weights(sc["pos"][v0:v1], sc["nrm"][v0:v1], sc["occ_c"], sc["occ_r"], H, W,
+                                    device="cuda", dtype=torch.float32, chunk=4096, cosine=False).contiguous()
+        vis[v0:v1] = hs.haar_forward(w)
+    prm = hs.haar_normal_rotations(torch.tensor(f32(sc["nrm"]), **dev))
+    got = hs.haar_shade_triple(H, W, torch.tensor(light, **dev), torch.tensor(brdf, **dev), prm, vis).cpu().numpy()
+    assert np.isfinite(got).all()
+    pick = np.sort(np.random.default_rng(5).choice(V, 12, replace=False))
+    vis_np = vis[torch.tensor(pick, device="cuda")].double().cpu().numpy()
+    ref = otr.shade_triple(light, brdf, f32(sc["nrm"])[pick], vis_np, H, W)
+    assert np.linalg.norm(got[pick] - ref) / np.linalg.norm(ref) <= 1e-4
