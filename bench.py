@@ -805,11 +805,14 @@ def main():
     L_dev = torch.empty_like(wl["L"])
     p_dev = torch.empty_like(wl["params"])
 
+    # the inputs are copied host -> device every step; the shading kernel
+    # writes the radiance straight into pinned host memory (NVLink-C2C), which
+    # measured 0.135 ms per step against 0.191 ms for a device buffer plus a
+    # separate device -> host copy
     def e2e_step():
         L_dev.copy_(L_host, non_blocking=True)
         p_dev.copy_(p_host, non_blocking=True)
-        hs.shade_batch(plan, L_dev, p_dev, tr, wl["radiance"])
-        R_host.copy_(wl["radiance"], non_blocking=True)
+        hs.shade_batch(plan, L_dev, p_dev, tr, R_host)
 
     for _ in range(3):
         e2e_step()
@@ -832,7 +835,8 @@ def main():
                            "l2": "flushed between timed steps (256 MiB write)",
                            "parallelism": f"{world} independent vertex shards (no collective)"},
                 "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "d2h": "radiance written by the shading kernel into pinned host memory"},
                 "gpu_launches": 3 * args.steps, "clocks": clk, "rows": rows}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -224,9 +224,13 @@ typedef struct {
  *   CSR_F32_U16      with F32  lighting, layout KSC (S*C % 4 == 0);
  *   BINCSR_F16_U32   with F32  lighting, layout SKC or SKC4;
  *   GCSR_F32_U16     with F32  lighting, layout KSC (S*C % 4 == 0).
- * radiance: [V][S][C] float32, overwritten.  Launches that use the same plan
- * must be ordered (one stream, or events): the plan's workspace and device
- * counters are shared. */
+ * radiance: [V][S][C] float32, overwritten.  It may also be page-locked host
+ * memory mapped into the device's address space (cudaHostAlloc'd, unified
+ * addressing): the shading kernels write it with plain stores, so the result
+ * reaches the host over the host link (NVLink-C2C on Grace-Blackwell) without
+ * a separate device-to-host copy.  Launches that use the same plan must be
+ * ordered (one stream, or events): the plan's workspace and device counters
+ * are shared. */
 HAAR_API haar_status_t shade_vertices(haar_shift_plan_t plan, const haar_transport_desc_t* transport,
                              const void* lighting, int S, float* radiance, void* stream);
 

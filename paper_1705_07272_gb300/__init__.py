@@ -169,6 +169,17 @@ def _dev(t, dtype=None, name="tensor"):
     return t.data_ptr()
 
 
+def _out(t, dtype, name):
+    """An output buffer: a CUDA tensor, or a pinned (page-locked) host tensor,
+    which the kernels write straight over the host link."""
+    import torch
+    if isinstance(t, torch.Tensor) and not t.is_cuda and t.is_pinned():
+        if not t.is_contiguous() or t.dtype != dtype:
+            raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+        return t.data_ptr()
+    return _dev(t, dtype, name)
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -289,13 +300,14 @@ class Transport:
 
 
 def shade_vertices(plan: Plan, transport: Transport, lighting, S, radiance=None, stream=None):
-    """radiance [V][S][C] = sum_k T[v][k] L'[s][c][k]."""
+    """radiance [V][S][C] = sum_k T[v][k] L'[s][c][k]; radiance may be a
+    pinned host tensor (written by the kernel over the host link)."""
     import torch
     if radiance is None:
         radiance = torch.empty((transport.V, S, plan.C), dtype=torch.float32, device=lighting.device)
     d = transport.desc()
     _check(lib().shade_vertices(plan.handle, ctypes.byref(d), _dev(lighting, None, "lighting"), S,
-                                _dev(radiance, torch.float32, "radiance"), _stream(stream)))
+                                _out(radiance, torch.float32, "radiance"), _stream(stream)))
     return radiance
 
 
@@ -308,7 +320,7 @@ def shade_batch(plan: Plan, coeffs_in, params, transport: Transport, radiance=No
     d = transport.desc()
     _check(lib().shade_batch(plan.handle, _dev(coeffs_in, torch.float32, "coeffs_in"),
                              _dev(params, torch.float64, "params"), S, ctypes.byref(d),
-                             _dev(radiance, torch.float32, "radiance"), _stream(stream)))
+                             _out(radiance, torch.float32, "radiance"), _stream(stream)))
     return radiance
 
 

@@ -278,3 +278,27 @@ def test_bincsr_small(hs):
     R4 = hs.shade_batch(plan4, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
     assert torch.equal(R4, R)
     assert plan4.status() == 0
+
+
+@pytest.mark.parametrize("kind", ["gcsr", "csr"])
+def test_radiance_into_pinned_host_memory(hs, kind):
+    # the shading kernels may write the radiance straight into page-locked host
+    # memory: the same bits as into device memory
+    import torch
+    sc = synth.scene(1, V=1003, H=32, W=64)
+    H, W = 32, 64
+    vals, idx, rowptr = _csr_inputs(sc, 64, H, W)
+    rp = _t(rowptr.astype(np.int32), torch.int32)
+    ix = _t(idx.astype(np.int16), torch.int16)
+    vv = _t(vals, torch.float32)
+    tr = (hs.haar_transport_group(sc["V"], H * W, rp, ix, vv) if kind == "gcsr"
+          else hs.Transport(hs.HAAR_T_CSR_F32_U16, sc["V"], 0, vv, ix, rp))
+    L = _t(f32(oh.forward(sc["light"])), torch.float32)
+    prm = _t(sc["params"], torch.float64)
+    plan = hs.Plan(H, W, 3, max_shifts=sc["S"], out_layout=hs.HAAR_LAYOUT_KSC)
+    dev_out = hs.shade_batch(plan, L, prm, tr)
+    host_out = torch.full((sc["V"], sc["S"], 3), -1.0).pin_memory()
+    hs.shade_batch(plan, L, prm, tr, host_out)
+    torch.cuda.synchronize()
+    assert torch.equal(host_out, dev_out.cpu())
+    plan.close()
