@@ -554,8 +554,9 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
   const int i0 = tr * T + 4 * by, j0 = tc * T + 4 * bx;
   const int Wm = g.W - 1;
   const int g1 = g.q << (2 * (g.n - 1));
+  // the fast path stores 8-byte vectors: the output must be 8-byte aligned
   const bool fast = OUT == HAAR_OUT_F32 && a.st_k == 1 && a.scale == 1.0f && (p == nullptr || p->perm_mask == 0u) &&
-                    4 * g1 <= a.K && g.n >= 2;
+                    4 * g1 <= a.K && g.n >= 2 && (reinterpret_cast<uintptr_t>(a.out) & 7) == 0;
   const float hsc = fast ? 0.5f : 1.0f;
 
   float a2[CG];

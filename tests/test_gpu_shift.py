@@ -337,3 +337,21 @@ def test_whole_map_kernel_layouts_and_truncation(hs):
         assert np.array_equal(o, base)
     o, _ = _run(hs, c, H, W, 0, prm, SPH, 0, hs.HAAR_LAYOUT_SKC, K=1000)
     assert np.array_equal(o, base[..., :1000])
+
+
+def test_output_not_16_byte_aligned(hs):
+    # an output one float past a 16-byte boundary takes the scalar store path:
+    # the same values as an aligned output
+    import torch
+    H, W = 64, 128
+    c = _lighting(3, H, W, 5)
+    prm = np.asarray(synth.translations(np.random.default_rng(5), 6, 128.0, 64.0), dtype=np.float64)
+    plan = hs.Plan(H, W, 3, max_shifts=6)
+    cin = torch.tensor(c, dtype=torch.float32, device="cuda")
+    pt = torch.tensor(prm, device="cuda")
+    ref = hs.haar_shift(plan, cin, pt)
+    buf = torch.zeros(ref.numel() + 1, dtype=torch.float32, device="cuda")
+    out = buf[1:].view(ref.shape)
+    hs.haar_shift(plan, cin, pt, out)
+    assert torch.equal(out, ref)
+    plan.close()
