@@ -110,49 +110,55 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// One CTA per vertex: both factors' rows arrive in shared memory by two bulk
-// copies, then the squares are visited level by level from the coarsest, the
-// factors' means for the next level written as they go.
-template <int C, int T>
+// One CTA per vertex: the squares are visited level by level from the
+// coarsest, the factors' means for the next level written as they go.  With
+// STAGED both factors' rows first arrive in shared memory by two bulk copies
+// (one latency per vertex); without it (maps whose rows would leave too few
+// CTAs per SM) each level's details are read straight from global memory,
+// coalesced, and shared memory holds only the means.
+template <int C, int T, bool STAGED>
 __global__ void __launch_bounds__(T) k_triple(TripleArgs a) {
   extern __shared__ __align__(16) float sm[];
-  float* sb = sm;                      // [N] BRDF row
-  float* sc = sm + a.N;                // [N] visibility row
-  float* mb = sc + a.N;                // [Nm] BRDF means
-  float* mc = mb + a.Nm;               // [Nm] visibility means
+  float* mb = sm + (STAGED ? 2 * a.N : 0);   // [Nm] BRDF means
+  float* mc = mb + a.Nm;                     // [Nm] visibility means
   __shared__ __align__(8) unsigned long long bar;
   __shared__ int abort_flag;
   __shared__ float red[T / 32][C];
   const int v = blockIdx.x, t = threadIdx.x;
-  const uint32_t b32 = tc::smem_u32(&bar);
-  if (t == 0) {
-    abort_flag = 0;
-    tc::mbar_init(b32, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const float* sb = STAGED ? sm : a.brdf + (long long)v * a.sb;        // BRDF row
+  const float* sc = STAGED ? sm + a.N : a.vis + (long long)v * a.sv;   // visibility row
+  if (STAGED) {
+    const uint32_t b32 = tc::smem_u32(&bar);
+    if (t == 0) {
+      abort_flag = 0;
+      tc::mbar_init(b32, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0) {
+      const uint32_t bytes = (uint32_t)a.N * 4u;
+      tc::mbar_arrive_tx(b32, 2u * bytes);
+      bulk_g2s(tc::smem_u32(sm), a.brdf + (long long)v * a.sb, bytes, b32);
+      bulk_g2s(tc::smem_u32(sm + a.N), a.vis + (long long)v * a.sv, bytes, b32);
+    }
+    bool ok = true;
+    if (t < 32) ok = tc::mbar_wait(b32, 0, a.status, &abort_flag);   // one warp polls, the rest sleep
+    if (!__syncthreads_and(ok)) {
+      if (t < C) a.out[(long long)v * C + t] = __int_as_float(0x7fc00000);
+      return;
+    }
   }
-  __syncthreads();
-  if (t == 0) {
-    const uint32_t bytes = (uint32_t)a.N * 4u;
-    tc::mbar_arrive_tx(b32, 2u * bytes);
-    bulk_g2s(tc::smem_u32(sb), a.brdf + (long long)v * a.sb, bytes, b32);
-    bulk_g2s(tc::smem_u32(sc), a.vis + (long long)v * a.sv, bytes, b32);
-  }
-  bool ok = true;
-  if (t < 32) ok = tc::mbar_wait(b32, 0, a.status, &abort_flag);   // one warp polls, the rest sleep
-  if (!__syncthreads_and(ok)) {
-    if (t < C) a.out[(long long)v * C + t] = __int_as_float(0x7fc00000);
-    return;
-  }
+  auto ld = [](const float* p, int i) { return STAGED ? p[i] : __ldg(p + i); };
   float acc[C];
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
   const float invH = 1.0f / (float)a.H;
   for (int k = t; k < a.q; k += T) {          // three scaling functions
-    const float bc = sb[k] * sc[k];
+    const float bk = ld(sb, k), ck = ld(sc, k), bc = bk * ck;
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) acc[ch] += __ldg(a.light + (long long)ch * a.N + k) * bc * invH;
-    mb[k] = sb[k] * invH;
-    mc[k] = sc[k] * invH;
+    mb[k] = bk * invH;
+    mc[k] = ck * invH;
   }
   __syncthreads();
   const int logW = 31 - __clz(a.W);
@@ -160,8 +166,8 @@ __global__ void __launch_bounds__(T) k_triple(TripleArgs a) {
     const int g = a.q << (2 * (a.n - l)), cols = a.W >> l, lc = logW - l, moff = mean_off(g, a.q);
     const float invB = 1.0f / (float)(1 << l);
     for (int k = t; k < g; k += T) {
-      const float bH = sb[g + k], bV = sb[2 * g + k], bD = sb[3 * g + k];
-      const float cH = sc[g + k], cV = sc[2 * g + k], cD = sc[3 * g + k];
+      const float bH = ld(sb, g + k), bV = ld(sb, 2 * g + k), bD = ld(sb, 3 * g + k);
+      const float cH = ld(sc, g + k), cV = ld(sc, 2 * g + k), cD = ld(sc, 3 * g + k);
       const float mbk = mb[moff + k], mck = mc[moff + k];
       // the factors' products that do not involve the lighting
       const float x1 = (bV * cD + bD * cV) * invB, x2 = (bH * cD + bD * cH) * invB, x3 = (bH * cV + bV * cH) * invB;
@@ -485,11 +491,19 @@ static haar_status_t launch_triple_c(const TripleArgs& a, float* ma, cudaStream_
   k_triple_means<<<C, 256, 0, st>>>(a, ma, const_cast<float4*>(a.pk));
   haar_status_t r = cuda_check(cudaGetLastError(), "k_triple_means launch");
   if (r != HAAR_OK) return r;
-  // 128 threads at every size: at 64 x 128 shared memory allows 2 CTAs per
-  // SM, and 256 threads per CTA measured slower (1.62 against 1.37 ms)
-  cudaError_t e = cudaFuncSetAttribute(k_triple<C, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_check(e, "k_triple attribute");
-  k_triple<C, 128><<<a.V, 128, smem, st>>>(a);
+  // up to 2048 coefficients both rows are staged by bulk copies; above, the
+  // staged rows would leave 2 CTAs per SM, so the details stream from memory
+  cudaError_t e;
+  if (a.N <= 2048) {
+    e = cudaFuncSetAttribute(k_triple<C, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(e, "k_triple attribute");
+    k_triple<C, 128, true><<<a.V, 128, smem, st>>>(a);
+  } else {
+    const size_t smem_m = 2 * (size_t)a.Nm * sizeof(float);
+    e = cudaFuncSetAttribute(k_triple<C, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
+    if (e != cudaSuccess) return cuda_check(e, "k_triple attribute");
+    k_triple<C, 128, false><<<a.V, 128, smem_m, st>>>(a);
+  }
   return cuda_check(cudaGetLastError(), "k_triple launch");
 }
 
