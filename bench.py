@@ -794,13 +794,15 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic_record(kname), "kernel": kname, "peak_source": peak_src,
                 "algorithmic_bytes": ab[kname], "kernel_ms": kms,
-                # what binds it: every group-CSR entry gathers one lighting row
-                # (S C floats) from the L2-resident lighting
-                "l2_row_gather_bytes": wl["union"] * wl["S"] * wl["C"] * 4,
-                "l2_row_gather_gbs": wl["union"] * wl["S"] * wl["C"] * 4 / (kms * 1e-3) / 1e9,
                 "other_kernels_ms": {"k_setup+k_shift": shift_avg, "k_shade_gcsr_f32": shade_avg},
                 "plain_csr_kernel": {"kernel": "k_shade_csr_f32", "ms": csr_avg,
                                      "achieved_gbs": ab["k_shade_csr_f32"] / (csr_avg * 1e-3) / 1e9}}
+    if kname == "k_shade_gcsr_f32":
+        # what binds it: every group-CSR entry gathers one lighting row (S C
+        # floats) from the L2-resident lighting
+        gb = wl["union"] * wl["S"] * wl["C"] * 4
+        roofline["l2_row_gather_bytes"] = gb
+        roofline["l2_row_gather_gbs"] = gb / (kms * 1e-3) / 1e9
 
     # end to end through the public API with host buffers
     L_host = wl["L"].cpu().pin_memory()
