@@ -499,6 +499,9 @@ static haar_status_t launch_triple_c(const TripleArgs& a, float* ma, cudaStream_
     if (e != cudaSuccess) return cuda_check(e, "k_triple attribute");
     k_triple<C, 128, true><<<a.V, 128, smem, st>>>(a);
   } else {
+    // (4 vertices per CTA sharing each square's lighting loads measured
+    // slower, 1.56 against 1.27 ms: the kernel is latency-bound, not bound by
+    // the lighting's L2 traffic)
     const size_t smem_m = 2 * (size_t)a.Nm * sizeof(float);
     e = cudaFuncSetAttribute(k_triple<C, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
     if (e != cudaSuccess) return cuda_check(e, "k_triple attribute");
