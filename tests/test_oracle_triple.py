@@ -142,3 +142,43 @@ def test_shade_triple_matches_rotating_in_pixel_space():
         for ch in range(2):
             ref = (haar.inverse(light[ch], H, W) * Bm * haar.inverse(vis[v], H, W)).sum()
             assert np.isclose(got[v, ch], ref, rtol=1e-12, atol=1e-12)
+
+
+def _golden_cases():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tripling_coefficients.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return {case: value for case, value in rows}
+
+
+def test_tripling_values_match_the_papers_statement():
+    # the paper's values are for the unit square; on an H x H pixel map the
+    # oracle's unit-pixel measure gives C_pixel = C_paper / H, and a square of
+    # side B pixels is the paper's level l = log2(H / B)
+    golden = _golden_cases()
+    assert golden == {"a": "1", "b": "2^l", "c": "+-2^l"}
+    H = W = 8
+    C = triple.tripling_coefficients(H, W) * H
+    N = H * W
+    seen = set()
+    for i in range(N):
+        for j in range(N):
+            for k in range(N):
+                v = C[i, j, k]
+                if abs(v) < 1e-12:
+                    continue
+                d = [haar.decode(H, W, x) for x in (i, j, k)]
+                if all(x[1] == -1 for x in d):                             # case a
+                    assert abs(v - 1.0) < 1e-12
+                    seen.add("a")
+                elif i != j and j != k and i != k and len({(x[0], x[2], x[3]) for x in d}) == 1:   # case b
+                    lvl = int(round(math.log2(H / (1 << d[0][0]))))
+                    assert abs(v - 2.0 ** lvl) < 1e-12
+                    seen.add("b")
+                else:                                                        # case c
+                    # the third function is the one that differs from the repeated pair
+                    third = d[2] if i == j else (d[1] if i == k else d[0])
+                    lvl = 0 if third[1] == -1 else int(round(math.log2(H / (1 << third[0]))))
+                    assert abs(abs(v) - 2.0 ** lvl) < 1e-12, (i, j, k, v)
+                    seen.add("c")
+    assert seen == {"a", "b", "c"}
