@@ -160,14 +160,20 @@ HAAR_API haar_status_t haar_shift(haar_shift_plan_t plan, const float* coeffs_in
  * and calls no cudaMalloc, cudaFree or allocating library routine: its
  * scratch is one fixed array of 2 Mi floats (8 MiB) in the library's device
  * memory, which every GPU that loads the library holds until the process
- * exits.  A call needs C*H*W + 2*(H+W) + S*(20 + C*T + 1) floats, T = H*W/4096
- * tiles for H >= 64 (1 or 2 below), each part rounded up to 64; larger calls
- * are rejected with HAAR_ERR_INVALID_ARG and a message giving both sizes
- * (RGB 256x512 fits with up to several thousand shifts; RGB 1024x2048 does
- * not fit).
+ * exits.  A call needs, each part rounded up to a multiple of 64 floats:
+ * the pixel map (C*H*W floats for translations, 8*H*W*ceil(C/3) for
+ * rotations), 8*H + 4*W floats of tables, for rotations S*8*(H+W) floats of
+ * per-rotation tables, 20*S floats of shift records, S*C*T floats of tile
+ * means (T = H*W/4096 tiles for H >= 64, 1 or 2 below; T = H*W/256 for
+ * float32 KSC translations) and S tile counters, for the map the shift runs
+ * on (H, W after start_level).  So RGB 256x512 takes up to 166 rotations or
+ * ~14 500 SCK translations, RGB 128x256 up to ~4 900 KSC translations, and
+ * RGB 1024x2048 does not fit.  Larger calls are rejected with
+ * HAAR_ERR_INVALID_ARG and a message giving both sizes.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life
+ * of the process (a device reset after that first call is not supported);
+ * make that first call before any stream capture.  Every call on a device shares the one array
  * and it keeps the previous call's contents (the call clears the tile
  * counters it needs at zero itself): calls that overlap on the GPU (other
  * streams, other host threads) race and give wrong results; order them.

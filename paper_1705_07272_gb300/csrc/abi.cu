@@ -21,6 +21,8 @@ haar_status_t set_error(haar_status_t st, const char* fmt, ...) {
   return st;
 }
 
+void clear_error() { g_err[0] = 0; }
+
 haar_status_t cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return HAAR_OK;
   cudaGetLastError();  // a non-sticky failure must not surface again at the next launch
@@ -49,6 +51,7 @@ static void free_plan(haar_shift_plan_s* p) {
   if (!p) return;
   cudaFree(p->pix);
   cudaFree(p->trig);
+  cudaFree(p->rtab);
   cudaFree(p->prm);
   cudaFree(p->means);
   cudaFree(p->counters);
@@ -123,8 +126,10 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
   const size_t light_bytes =
       p->light_elems * out_elem_bytes(d->out_type) * (d->out_type == HAAR_OUT_BF16_HILO ? 2 : 1);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&p->pix, sizeof(float) * g.N * g.C);
-  if (e == cudaSuccess) e = cudaMalloc(&p->trig, sizeof(float) * 2 * (g.H + g.W));
+  if (e == cudaSuccess) e = cudaMalloc(&p->pix, sizeof(float) * pix_floats(d->kind, g.H, g.W, g.C));
+  if (e == cudaSuccess) e = cudaMalloc(&p->trig, sizeof(float) * trig_floats(g.H, g.W));
+  if (e == cudaSuccess && (d->kind == HAAR_SHIFT_ROTATE || d->kind == HAAR_SHIFT_ROTATE_EULER))
+    e = cudaMalloc(&p->rtab, sizeof(float4) * rot_table_float4s(g.H, g.W) * S);
   if (e == cudaSuccess) e = cudaMalloc(&p->prm, sizeof(ShiftParam) * S);
   p->means_cap = S * g.C * g.n_tiles;
   if (ksc_eligible(*d, g, (int)S) && ksc_means_floats(g, (int)S) > p->means_cap)

@@ -21,7 +21,8 @@ struct ShiftParam {
   uint32_t perm_mask;        // bit l (1..n): level l is a signed permutation; bit n+1: scaling
   int pad;
   float R[9];                // rotation p' = R p (row-major), float32
-  float pad2[3];
+  float a_px;                // rotations: a / dphi - 1/2 for R = Ry(a) Rx(b) Ry(c) (picks anchor columns)
+  float pad2[2];
 };
 static_assert(sizeof(ShiftParam) == 80, "ShiftParam layout");
 
@@ -69,7 +70,8 @@ struct haar_shift_plan_s {
   int device;
   // workspace (device)
   float* pix;                // [C][H][W] pixel map synthesised per launch
-  float* trig;               // sin_t[H] cos_t[H] sin_p[W] cos_p[W]
+  float* trig;               // rotation tables of the map: see trig_floats()
+  float* rtab;               // rotation kinds: per-rotation tables [max_shifts][rot_table_float4s] float4
   hs::ShiftParam* prm;       // [max_shifts]
   float* means;              // [max_shifts][C][n_tiles] (or [max_shifts][C][H W / 256] for the KSC kernel)
   size_t means_cap;          // floats in means
@@ -82,18 +84,30 @@ struct haar_shift_plan_s {
 
 namespace hs {
 
-// atan2(y, x) in [-pi, pi] for the rotation coordinates: reduction to
-// t = min(|x|, |y|) / max(|x|, |y|) in [0, 1], atan(t) = t P(t^2) with P of
-// degree 7 (coefficients from a least-squares fit on [0, 1] reweighted
-// towards its largest errors: |error| < 1.5e-7 rad when evaluated in FP32,
-// i.e. < 2e-5 pixel at 512 columns), then the reflections atan(y/x) =
-// pi/2 - atan(x/y) and the half-plane x < 0.  (0, 0) gives 0.
+// Rotation tables of a map (plan->trig, floats): [H] float4 (sin theta_i hi,
+// lo, cos theta_i hi, lo), then FP64 sin theta_i [H], cos theta_i [H],
+// sin phi_j [W], cos phi_j [W].
+__host__ __device__ __forceinline__ long long trig_floats(int H, int W) { return 4LL * H + 4LL * (H + W); }
+// Per-rotation tables (float4): sin/cos psi_j [W], sin/cos alpha_m [W], rows [2H].
+__host__ __device__ __forceinline__ long long rot_table_float4s(int H, int W) { return 2LL * W + 2LL * H; }
+// Pixel map floats the set-up synthesises: rotations read an interleaved map
+// [ceil(C/3)][H][W][8] (each texel holds three channels at columns j and j+1).
+__host__ __device__ __forceinline__ long long pix_floats(int kind, int H, int W, int C) {
+  const long long N = (long long)H * W;
+  return (kind == HAAR_SHIFT_ROTATE || kind == HAAR_SHIFT_ROTATE_EULER) ? 8LL * N * ((C + 2) / 3) : N * C;
+}
+
+// atan2(y, x) in [-pi, pi]: reduction to t = min(|x|, |y|) / max(|x|, |y|)
+// in [0, 1], atan(t) = t P(t^2) with P of degree 7 (Lawson's minimax fit,
+// tests/atan_fit.py: |error| < 1.5e-7 rad when evaluated in FP32), then the
+// reflections atan(y/x) = pi/2 - atan(x/y) and the half-plane x < 0.  (0, 0)
+// gives 0.
 __device__ __forceinline__ float rot_atan2(float y, float x) {
   const float ax = fabsf(x), ay = fabsf(y);
   const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
   const float t = (mx > 0.0f) ? __fdividef(mn, mx) : 0.0f;
   const float u = t * t;
-  constexpr float P[8] = {9.999993443e-01f, -3.332985938e-01f, 1.994656622e-01f, -1.390863210e-01f, 9.642205387e-02f, -5.591243505e-02f, 2.186303213e-02f, -4.054587334e-03f};
+  constexpr float P[8] = {9.999993356e-01f, -3.332986071e-01f, 1.994656467e-01f, -1.390862427e-01f, 9.642182932e-02f, -5.591211863e-02f, 2.186280589e-02f, -4.054523135e-03f};
   float p = P[7];
 #pragma unroll
   for (int i = 6; i >= 0; --i) p = fmaf(p, u, P[i]);
@@ -167,6 +181,7 @@ __device__ __forceinline__ float2 u2f(unsigned long long a) {
 
 // status helpers (abi.cu)
 haar_status_t set_error(haar_status_t st, const char* fmt, ...);
+void clear_error();
 haar_status_t cuda_check(cudaError_t e, const char* what);
 bool injected(const char* entry);
 

@@ -34,6 +34,7 @@ using namespace hs;
 
 extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const float* cin, const double* params,
                                             int S, void* out, void* stream) {
+  clear_error();
   if (injected("haar_shift_noalloc")) return set_error(HAAR_ERR_INJECTED, "haar_shift_noalloc: injected fault");
   if (d == nullptr || cin == nullptr || params == nullptr || out == nullptr)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: null argument");
@@ -41,7 +42,7 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   if (d->height < 2 || d->height > 4096 || (d->height & (d->height - 1)) != 0 ||
       (d->width != d->height && d->width != 2 * d->height))
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: unsupported map %dx%d", d->height, d->width);
-  if (d->start_level < 0 || (d->height >> d->start_level) < 2)
+  if (d->start_level < 0 || d->start_level > 12 || (d->height >> d->start_level) < 2)
     return set_error(HAAR_ERR_INVALID_ARG, "haar_shift_noalloc: start_level %d leaves a map smaller than 2 x 2",
                      d->start_level);
   const int H = d->height >> d->start_level, W = d->width >> d->start_level;   // the map the shift runs on
@@ -63,19 +64,22 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
 
   // scratch layout (floats, each region 256-byte aligned)
   const Geometry g = make_geometry(H, W, C, d->boundary, choose_tile(H, W, C, S));
-  const size_t n_pix = round64((size_t)C * N);
-  const size_t n_trig = round64(2 * (size_t)(H + W));
+  const bool rot = d->kind == HAAR_SHIFT_ROTATE || d->kind == HAAR_SHIFT_ROTATE_EULER;
+  const size_t n_pix = round64((size_t)pix_floats(d->kind, H, W, C));
+  const size_t n_trig = round64((size_t)trig_floats(H, W));
+  const size_t n_rtab = rot ? round64((size_t)S * 4 * rot_table_float4s(H, W)) : 0;
   const size_t n_prm = round64((size_t)S * sizeof(ShiftParam) / sizeof(float));
   size_t n_means = round64((size_t)S * C * g.n_tiles);
   if (ksc_eligible(*d, g, S) && round64(ksc_means_floats(g, S)) > n_means) n_means = round64(ksc_means_floats(g, S));
   const size_t n_cnt = round64((size_t)S);
-  const size_t need = n_pix + n_trig + n_prm + n_means + n_cnt;
+  const size_t need = n_pix + n_trig + n_rtab + n_prm + n_means + n_cnt;
   if (need > kNoAllocFloats)
     return set_error(HAAR_ERR_INVALID_ARG,
-                     "haar_shift_noalloc: needs %zu scratch floats (C*H*W + tables for S = %d shifts), the fixed "
-                     "maximum is %zu", need, S, kNoAllocFloats);
+                     "haar_shift_noalloc: needs %zu scratch floats (pixel map, tables and S = %d shift records), "
+                     "the fixed maximum is %zu", need, S, kNoAllocFloats);
 
-  // once per device: the device address of the scratch array
+  // once per device: the device address of the scratch array (kept for the
+  // life of the process; a device reset after the first call is not supported)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_check(e, "haar_shift_noalloc: cudaGetDevice");
@@ -101,12 +105,19 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   p.cin_stride = (long long)d->height * d->width;
   p.pscale = 1.0 / (double)(1 << d->start_level);
   p.device = dev;
-  p.pix = base;
-  p.trig = base + n_pix;
-  p.prm = reinterpret_cast<ShiftParam*>(base + n_pix + n_trig);
-  p.means = base + n_pix + n_trig + n_prm;
+  float* q = base;
+  p.pix = q;
+  q += n_pix;
+  p.trig = q;
+  q += n_trig;
+  p.rtab = rot ? q : nullptr;
+  q += n_rtab;
+  p.prm = reinterpret_cast<ShiftParam*>(q);
+  q += n_prm;
+  p.means = q;
   p.means_cap = n_means;
-  p.counters = reinterpret_cast<unsigned*>(base + n_pix + n_trig + n_prm + n_means);
+  q += n_means;
+  p.counters = reinterpret_cast<unsigned*>(q);
   cudaStream_t st = (cudaStream_t)stream;
   haar_status_t r = HAAR_OK;
   if (d->kind != HAAR_SHIFT_TRANSLATE) r = launch_trig(&p, st);     // tables of this call's map

@@ -17,6 +17,7 @@
 #include <stdio.h>
 
 #include "common.cuh"
+#include "rotcoord.cuh"
 
 namespace hs {
 
@@ -37,10 +38,34 @@ struct ShiftArgs {
   const ShiftParam* prm;  // [S] or null
   float* means;           // [S][C][n_tiles] (null: means go to out[..., 0:n_tiles])
   unsigned* counters;     // [S] (null: no in-kernel coarse pass)
-  const float* trig;      // sin_t[H] cos_t[H] sin_p[W] cos_p[W]
+  const float4* rows;     // rotations: [H] (sin theta_i hi, lo, cos theta_i hi, lo)
+  const float4* rtab;     // rotations: per-rotation tables, rt_stride float4 apart
+  long long rt_stride;
   float scale;
   float u_scale, v_scale; // H/pi, W/(2 pi)
 };
+
+// The two row taps of a rotated sample as texel offsets into the interleaved
+// rotation map (each texel holds columns c and c + 1): rows beyond a pole are
+// the mirrored row half a turn away (SPHERE) or wrap (TORUS).
+__device__ __forceinline__ void rot_taps(const RotSrc& o, int H, int W, int boundary, int& t0, int& t1) {
+  int r0 = o.r, r1 = o.r + 1, h0 = 0, h1 = 0;
+  if (boundary == HAAR_BOUNDARY_TORUS) {
+    r0 &= H - 1;
+    r1 &= H - 1;
+  } else {
+    if (r0 < 0) { r0 = 0; h0 = W >> 1; }
+    if (r1 >= H) { r1 = H - 1; h1 = W >> 1; }
+  }
+  t0 = r0 * W + ((o.c + h0) & (W - 1));
+  t1 = r1 * W + ((o.c + h1) & (W - 1));
+}
+
+// Bilinear value of channel ci (0..2) of a texel pair (rows t0, t1).
+__device__ __forceinline__ float rot_lerp(float a0, float a1, float b0, float b1, float fu, float fv) {
+  const float top = fmaf(fv, a1 - a0, a0), bot = fmaf(fv, b1 - b0, b0);
+  return fmaf(fu, bot - top, top);
+}
 
 // ------------------------------------------------------------------ helpers
 
@@ -315,35 +340,21 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
       }
     } else if (KIND == KIND_ROTATE) {
       __syncthreads();
+      const float4* rt = a.rtab + (long long)s * a.rt_stride;
+      const float4* tex = reinterpret_cast<const float4*>(a.pix) + (long long)cgrp * g.N * 2;
       for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
         const int ii = e / T, jj = e - ii * T;
         const int i = i_org + ii, j = j_org + jj;
-        const float st = __ldg(a.trig + i), ct = __ldg(a.trig + g.H + i);
-        const float sp = __ldg(a.trig + 2 * g.H + j), cp = __ldg(a.trig + 2 * g.H + g.W + j);
-        const float dx = st * sp, dy = ct, dz = st * cp;
-        const float px = fmaf(pr.R[0], dx, fmaf(pr.R[1], dy, pr.R[2] * dz));
-        const float py = fmaf(pr.R[3], dx, fmaf(pr.R[4], dy, pr.R[5] * dz));
-        const float pz = fmaf(pr.R[6], dx, fmaf(pr.R[7], dy, pr.R[8] * dz));
-        const float rho = sqrtf(fmaf(px, px, pz * pz));
-        const float th = rot_atan2(rho, py);
-        const float ph = rot_atan2(px, pz);
-        const float u = fmaf(th, a.u_scale, -0.5f);
-        const float v = fmaf(ph, a.v_scale, -0.5f);
-        const float fi = floorf(u), fj = floorf(v);
-        const float fu = u - fi, fv = v - fj;
-        int i0 = (int)fi, j0 = (int)fj;
-        int ia = i0, ja = j0, ib = i0, jb = j0 + 1, ic = i0 + 1, jc = j0, id = i0 + 1, jd = j0 + 1;
-        ext_index(ia, ja, g.H, g.W, g.boundary);
-        ext_index(ib, jb, g.H, g.W, g.boundary);
-        ext_index(ic, jc, g.H, g.W, g.boundary);
-        ext_index(id, jd, g.H, g.W, g.boundary);
-        const long long oa = (long long)ia * g.W + ja, ob = (long long)ib * g.W + jb;
-        const long long oc = (long long)ic * g.W + jc, od = (long long)id * g.W + jd;
-        for (int ci = 0; ci < cgn; ++ci) {
-          const float* F = a.pix + (long long)(c0 + ci) * g.N;
-          const float f00 = __ldg(F + oa), f01 = __ldg(F + ob), f10 = __ldg(F + oc), f11 = __ldg(F + od);
-          pbuf[ci * T * T + e] = (1.0f - fu) * ((1.0f - fv) * f00 + fv * f01) +
-                                 fu * ((1.0f - fv) * f10 + fv * f11);
+        const RotSrc o = rot_source(__ldg(a.rows + i), __ldg(rt + 2 * g.W + 2 * i), __ldg(rt + 2 * g.W + 2 * i + 1),
+                                    __ldg(rt + j), rt + g.W, a.rows, pr.a_px, a.u_scale, a.v_scale, g.H, g.W);
+        int t0, t1;
+        rot_taps(o, g.H, g.W, g.boundary, t0, t1);
+        const float4 p0 = __ldg(tex + 2 * t0), p1 = __ldg(tex + 2 * t1);
+        pbuf[e] = rot_lerp(p0.x, p0.y, p1.x, p1.y, o.fu, o.fv);
+        if (cgn > 1) pbuf[T * T + e] = rot_lerp(p0.z, p0.w, p1.z, p1.w, o.fu, o.fv);
+        if (cgn > 2) {
+          const float4 q0 = __ldg(tex + 2 * t0 + 1), q1 = __ldg(tex + 2 * t1 + 1);
+          pbuf[2 * T * T + e] = rot_lerp(q0.x, q0.y, q1.x, q1.y, o.fu, o.fv);
         }
       }
     } else {  // KIND_COPY: forward transform of maps [batch][H][W]
@@ -606,12 +617,11 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
     // row pairs: the two rows' 8 pixels per channel finish their two level-1
     // blocks at once, so only one row pair of pixels is live at a time
     const ShiftParam pr = *p;
-    float sp[4], cp[4];
+    const float4* rt = a.rtab + (long long)s * a.rt_stride;
+    const float4* tex = reinterpret_cast<const float4*>(a.pix) + (long long)cgrp * g.N * 2;
+    float4 ps[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sp[q] = __ldg(a.trig + 2 * g.H + j0 + q);
-      cp[q] = __ldg(a.trig + 2 * g.H + g.W + j0 + q);
-    }
+    for (int q = 0; q < 4; ++q) ps[q] = __ldg(rt + j0 + q);
     float A1[CG][4];
 #pragma unroll
     for (int rp = 0; rp < 2; ++rp) {
@@ -619,53 +629,20 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         const int i = i0 + 2 * rp + rr;
-        const float st = __ldg(a.trig + i), ct = __ldg(a.trig + g.H + i);
-        int off[4][4];
-        float fu[4], fv[4];
+        const float4 th = __ldg(a.rows + i), ab = __ldg(rt + 2 * g.W + 2 * i), cd = __ldg(rt + 2 * g.W + 2 * i + 1);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float dx = st * sp[q], dy = ct, dz = st * cp[q];
-          const float px = fmaf(pr.R[0], dx, fmaf(pr.R[1], dy, pr.R[2] * dz));
-          const float py = fmaf(pr.R[3], dx, fmaf(pr.R[4], dy, pr.R[5] * dz));
-          const float pz = fmaf(pr.R[6], dx, fmaf(pr.R[7], dy, pr.R[8] * dz));
-          const float rho = sqrtf(fmaf(px, px, pz * pz));
-          const float u = fmaf(rot_atan2(rho, py), a.u_scale, -0.5f);
-          const float v = fmaf(rot_atan2(px, pz), a.v_scale, -0.5f);
-          const float fi = floorf(u), fj = floorf(v);
-          fu[q] = u - fi;
-          fv[q] = v - fj;
-          const int ia = (int)fi, ja = (int)fj;
-          // taps: rows ia, ia+1 in [-1, H] (one step past a pole at most), columns cyclic
-          int r0 = ia, r1 = ia + 1, h0 = 0, h1 = 0;
-          if (g.boundary == HAAR_BOUNDARY_TORUS) {
-            r0 &= (g.H - 1);
-            r1 &= (g.H - 1);
-          } else {
-            if (r0 < 0) { r0 = -1 - r0; h0 = g.W >> 1; }
-            if (r0 >= g.H) { r0 = 2 * g.H - 1 - r0; h0 = g.W >> 1; }
-            if (r1 < 0) { r1 = -1 - r1; h1 = g.W >> 1; }
-            if (r1 >= g.H) { r1 = 2 * g.H - 1 - r1; h1 = g.W >> 1; }
-          }
-          off[q][0] = r0 * g.W + ((ja + h0) & Wm);
-          off[q][1] = r0 * g.W + ((ja + 1 + h0) & Wm);
-          off[q][2] = r1 * g.W + ((ja + h1) & Wm);
-          off[q][3] = r1 * g.W + ((ja + 1 + h1) & Wm);
-        }
-#pragma unroll
-        for (int ci = 0; ci < CG; ++ci) {
-          if (ci < cgn) {
-            const float* F = a.pix + (long long)(c0 + ci) * g.N;
-            float f[4][4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-              for (int t = 0; t < 4; ++t) f[q][t] = __ldg(F + off[q][t]);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float w0 = (1.0f - fu[q]) * hsc, w1 = fu[q] * hsc;
-              x[ci][4 * rr + q] = w0 * ((1.0f - fv[q]) * f[q][0] + fv[q] * f[q][1]) +
-                                  w1 * ((1.0f - fv[q]) * f[q][2] + fv[q] * f[q][3]);
-            }
+          const RotSrc o = rot_source(th, ab, cd, ps[q], rt + g.W, a.rows, pr.a_px, a.u_scale, a.v_scale, g.H, g.W);
+          int t0, t1;
+          rot_taps(o, g.H, g.W, g.boundary, t0, t1);
+          const float4 p0 = __ldg(tex + 2 * t0), p1 = __ldg(tex + 2 * t1);
+          const float w = hsc;
+          if (0 < cgn) x[0][4 * rr + q] = w * rot_lerp(p0.x, p0.y, p1.x, p1.y, o.fu, o.fv);
+          if (CG > 1 && 1 < cgn) x[CG > 1 ? 1 : 0][4 * rr + q] = w * rot_lerp(p0.z, p0.w, p1.z, p1.w, o.fu, o.fv);
+          if (CG > 2 && 2 < cgn) {
+            const float2 q0 = __ldg(reinterpret_cast<const float2*>(tex + 2 * t0 + 1));
+            const float2 q1 = __ldg(reinterpret_cast<const float2*>(tex + 2 * t1 + 1));
+            x[CG > 2 ? 2 : 0][4 * rr + q] = w * rot_lerp(q0.x, q0.y, q1.x, q1.y, o.fu, o.fv);
           }
         }
       }
@@ -975,8 +952,11 @@ __global__ void __launch_bounds__(kThreads) k_coarse_inplace(ShiftArgs a) {
 
 // Per-launch set-up: blocks [0, nbp) synthesise the pixel map from the
 // coefficients (inverse transform, one thread per pixel summing its
-// ancestors); the last block builds the shift records in FP64 and clears the
-// per-shift tile counters.
+// ancestors; for the rotation kinds one thread per texel of the interleaved
+// map, see pix_floats()).  Translations and the chain-rule route: the last
+// block builds the shift records in FP64 and clears the per-shift tile
+// counters.  Rotations: block nbp + s builds rotation s's record and its
+// tables in FP64 (the one-time construction of the shift's mixing weights).
 struct SetupArgs {
   int H, W, C, n, q, kind, boundary, S, nbp;
   long long cin_stride;   // floats between input channels (the full map's N)
@@ -986,6 +966,9 @@ struct SetupArgs {
   const double* params;
   ShiftParam* prm;
   unsigned* counters;
+  const double* dtrig;    // rotations: FP64 sin theta_i [H], cos theta_i [H], sin phi_j [W], cos phi_j [W]
+  float4* rtab;           // rotations: per-rotation tables
+  long long rt_stride;
 };
 
 __device__ __forceinline__ float synth_pixel(const float* cf, int i, int j, int W, int n, int q) {
@@ -1001,16 +984,118 @@ __device__ __forceinline__ float synth_pixel(const float* cf, int i, int j, int 
   return x;
 }
 
+__device__ __forceinline__ float4 split2(double s, double c) {
+  const float sh = (float)s, ch = (float)c;
+  return make_float4(sh, (float)(s - (double)sh), ch, (float)(c - (double)ch));
+}
+
+__device__ void rotation_matrix(const SetupArgs& a, int s, double R[9]) {
+  if (a.kind == HAAR_SHIFT_ROTATE) {
+    for (int k = 0; k < 9; ++k) R[k] = a.params[9 * s + k];
+    return;
+  }
+  const double al = a.params[3 * s], be = a.params[3 * s + 1], ga = a.params[3 * s + 2];
+  const double ca = cos(al), sa = sin(al), cb = cos(be), sb = sin(be);
+  const double cg = cos(ga), sg = sin(ga);
+  const double Rx[9] = {1, 0, 0, 0, ca, -sa, 0, sa, ca};
+  const double Ry[9] = {cb, 0, sb, 0, 1, 0, -sb, 0, cb};
+  const double Rz[9] = {cg, -sg, 0, sg, cg, 0, 0, 0, 1};
+  double M[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      M[3 * r + c] = Ry[3 * r] * Rx[c] + Ry[3 * r + 1] * Rx[3 + c] + Ry[3 * r + 2] * Rx[6 + c];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      R[3 * r + c] = Rz[3 * r] * M[c] + Rz[3 * r + 1] * M[3 + c] + Rz[3 * r + 2] * M[6 + c];
+}
+
 __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
   pdl_trigger();                                  // the shift kernel may be scheduled (it waits for this grid)
   const long long N = (long long)a.H * a.W;
+  const bool rot = a.kind == HAAR_SHIFT_ROTATE || a.kind == HAAR_SHIFT_ROTATE_EULER;
   if ((int)blockIdx.x < a.nbp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rot) {
+      // texel (group g, row i, column j): channels 3g..3g+2 at columns j and j+1
+      const int G = (a.C + 2) / 3;
+      if (e >= N * G) return;
+      const int gi = (int)(e / N);
+      const long long rem = e - (long long)gi * N;
+      const int i = (int)(rem / a.W), j = (int)(rem - (long long)i * a.W), j1 = (j + 1) & (a.W - 1);
+      float v[6];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int c = 3 * gi + t;
+        if (c < a.C) {
+          const float* cf = a.cin + (long long)c * a.cin_stride;
+          v[2 * t] = synth_pixel(cf, i, j, a.W, a.n, a.q);
+          v[2 * t + 1] = synth_pixel(cf, i, j1, a.W, a.n, a.q);
+        } else {
+          v[2 * t] = v[2 * t + 1] = 0.0f;
+        }
+      }
+      float4* o = reinterpret_cast<float4*>(a.pix) + 2 * e;
+      o[0] = make_float4(v[0], v[1], v[2], v[3]);
+      o[1] = make_float4(v[4], v[5], 0.0f, 0.0f);
+      return;
+    }
     if (e >= N * a.C) return;
     const int c = (int)(e / N);
     const long long rem = e - (long long)c * N;
     const int i = (int)(rem / a.W), j = (int)(rem - (long long)i * a.W);
     a.pix[e] = synth_pixel(a.cin + (long long)c * a.cin_stride, i, j, a.W, a.n, a.q);
+    return;
+  }
+  if (rot) {
+    // rotation s = blockIdx.x - nbp: R = Ry(a) Rx(b) Ry(c) (proper Euler
+    // angles), found without trigonometry: (sin a, cos a) from R's middle
+    // column, then M = Ry(-a) R = Rx(b) Ry(c) gives (cos c, sin c) from its
+    // first row and (sin b, cos b) from its middle column
+    const int s = blockIdx.x - a.nbp;
+    __shared__ double sh[6];
+    if (threadIdx.x == 0) {
+      double R[9];
+      rotation_matrix(a, s, R);
+      const double na = hypot(R[1], R[7]);
+      const double sa = na > 0.0 ? R[1] / na : 0.0, ca = na > 0.0 ? R[7] / na : 1.0;
+      const double m00 = ca * R[0] - sa * R[6], m02 = ca * R[2] - sa * R[8];
+      const double m11 = R[4], m21 = sa * R[1] + ca * R[7];
+      const double nc = hypot(m00, m02), nb = hypot(m21, m11);
+      sh[0] = sa; sh[1] = ca;
+      sh[2] = nb > 0.0 ? m21 / nb : 0.0; sh[3] = nb > 0.0 ? m11 / nb : 1.0;
+      sh[4] = nc > 0.0 ? m02 / nc : 0.0; sh[5] = nc > 0.0 ? m00 / nc : 1.0;
+      ShiftParam p;
+      p.kx = p.ky = 0;
+      p.wx0 = p.wy0 = 1.0f;
+      p.wx1 = p.wy1 = 0.0f;
+      p.perm_mask = 0u;
+      p.pad = 0;
+      for (int k = 0; k < 9; ++k) p.R[k] = (float)R[k];
+      p.a_px = (float)(atan2(sa, ca) * (a.W / (2.0 * 3.14159265358979323846)) - 0.5);
+      p.pad2[0] = p.pad2[1] = 0.0f;
+      a.prm[s] = p;
+      a.counters[s] = 0u;
+    }
+    __syncthreads();
+    const double sa = sh[0], ca = sh[1], sb = sh[2], cb = sh[3], sc = sh[4], cc = sh[5];
+    const double* st = a.dtrig;
+    const double* ct = a.dtrig + a.H;
+    const double* sp = a.dtrig + 2 * a.H;
+    const double* cp = sp + a.W;
+    float4* rt = a.rtab + (long long)s * a.rt_stride;
+    for (int j = threadIdx.x; j < a.W; j += blockDim.x) {
+      const double s0 = sp[j], c0 = cp[j];
+      rt[j] = split2(s0 * cc + c0 * sc, c0 * cc - s0 * sc);             // psi_j = phi_j + c
+      rt[a.W + j] = split2(s0 * ca - c0 * sa, c0 * ca + s0 * sa);       // alpha_j = phi_j - a
+    }
+    for (int i = threadIdx.x; i < a.H; i += blockDim.x) {
+      const double s0 = st[i], c0 = ct[i];
+      const double A = sb * c0, B = cb * s0, C = cb * c0, D = sb * s0;
+      float4* r = rt + 2 * a.W + 2 * i;
+      const float Ah = (float)A, Bh = (float)B, Ch = (float)C, Dh = (float)D;
+      r[0] = make_float4(Ah, (float)(A - (double)Ah), Bh, (float)(B - (double)Bh));
+      r[1] = make_float4(Ch, (float)(C - (double)Ch), Dh, (float)(D - (double)Dh));
+    }
     return;
   }
   for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
@@ -1021,7 +1106,8 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
     p.perm_mask = 0u;
     p.pad = 0;
     for (int k = 0; k < 9; ++k) p.R[k] = (k % 4 == 0) ? 1.0f : 0.0f;
-    p.pad2[0] = p.pad2[1] = p.pad2[2] = 0.0f;
+    p.a_px = 0.0f;
+    p.pad2[0] = p.pad2[1] = 0.0f;
     if (a.kind == HAAR_SHIFT_TRANSLATE) {
       const double dx = a.params[2 * s] * a.pscale, dy = a.params[2 * s + 1] * a.pscale;
       const double W = a.W;
@@ -1050,23 +1136,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
       }
     } else {
       double R[9];
-      if (a.kind == HAAR_SHIFT_ROTATE) {
-        for (int k = 0; k < 9; ++k) R[k] = a.params[9 * s + k];
-      } else {
-        const double al = a.params[3 * s], be = a.params[3 * s + 1], ga = a.params[3 * s + 2];
-        const double ca = cos(al), sa = sin(al), cb = cos(be), sb = sin(be);
-        const double cg = cos(ga), sg = sin(ga);
-        const double Rx[9] = {1, 0, 0, 0, ca, -sa, 0, sa, ca};
-        const double Ry[9] = {cb, 0, sb, 0, 1, 0, -sb, 0, cb};
-        const double Rz[9] = {cg, -sg, 0, sg, cg, 0, 0, 0, 1};
-        double M[9];
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c)
-            M[3 * r + c] = Ry[3 * r] * Rx[c] + Ry[3 * r + 1] * Rx[3 + c] + Ry[3 * r + 2] * Rx[6 + c];
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c)
-            R[3 * r + c] = Rz[3 * r] * M[c] + Rz[3 * r + 1] * M[3 + c] + Rz[3 * r + 2] * M[6 + c];
-      }
+      rotation_matrix(a, s, R);
       for (int k = 0; k < 9; ++k) p.R[k] = (float)R[k];
     }
     a.prm[s] = p;
@@ -1074,18 +1144,23 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
   }
 }
 
+// Rotation tables of the map (see trig_floats()): pixel-centre sines and
+// cosines in FP64, and the row ones also as float pairs.
 __global__ void k_trig(int H, int W, float* trig) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const double pi = 3.14159265358979323846;
+  double* d = reinterpret_cast<double*>(trig + 4LL * H);
   if (e < H) {
     const double t = (e + 0.5) * pi / H;
-    trig[e] = (float)sin(t);
-    trig[H + e] = (float)cos(t);
+    const double sn = sin(t), cs = cos(t);
+    reinterpret_cast<float4*>(trig)[e] = split2(sn, cs);
+    d[e] = sn;
+    d[H + e] = cs;
   } else if (e < H + W) {
     const int j = e - H;
     const double t = (j + 0.5) * 2.0 * pi / W;
-    trig[2 * H + j] = (float)sin(t);
-    trig[2 * H + W + j] = (float)cos(t);
+    d[2 * H + j] = sin(t);
+    d[2 * H + W + j] = cos(t);
   }
 }
 
@@ -1181,7 +1256,8 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
   a.kind = p->desc.kind;
   a.boundary = g.boundary;
   a.S = S;
-  const long long total = g.N * g.C;
+  const bool rot = a.kind == HAAR_SHIFT_ROTATE || a.kind == HAAR_SHIFT_ROTATE_EULER;
+  const long long total = rot ? g.N * ((g.C + 2) / 3) : g.N * g.C;
   a.nbp = (int)((total + kThreads - 1) / kThreads);
   a.cin = coeffs_in;
   a.cin_stride = p->cin_stride;
@@ -1190,7 +1266,11 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
   a.params = params;
   a.prm = p->prm;
   a.counters = p->counters;
-  k_setup<<<a.nbp + 1, kThreads, 0, st>>>(a);
+  a.dtrig = reinterpret_cast<const double*>(p->trig + 4LL * g.H);
+  a.rtab = reinterpret_cast<float4*>(p->rtab);
+  a.rt_stride = rot_table_float4s(g.H, g.W);
+  if (rot && p->rtab == nullptr) return set_error(HAAR_ERR_INVALID_ARG, "rotation tables missing");
+  k_setup<<<a.nbp + (rot ? S : 1), kThreads, 0, st>>>(a);
   return cuda_check(cudaGetLastError(), "k_setup launch");
 }
 
@@ -1230,7 +1310,9 @@ static haar_status_t launch_ksc(haar_shift_plan_s* p, const float* coeffs_in, in
   a.prm = p->prm;
   a.means = p->means;
   a.counters = p->counters;
-  a.trig = p->trig;
+  a.rows = nullptr;
+  a.rtab = nullptr;
+  a.rt_stride = 0;
   a.scale = 1.0f;
   a.u_scale = a.v_scale = 0.0f;
   const size_t sm = ksc_smem_floats(g.n_tiles) * sizeof(float);
@@ -1265,7 +1347,9 @@ haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, 
   a.prm = p->prm;
   a.means = p->means;
   a.counters = p->counters;
-  a.trig = p->trig;
+  a.rows = reinterpret_cast<const float4*>(p->trig);
+  a.rtab = reinterpret_cast<const float4*>(p->rtab);
+  a.rt_stride = rot_table_float4s(g.H, g.W);
   a.scale = 1.0f;
   a.u_scale = (float)(g.H / 3.14159265358979323846);
   a.v_scale = (float)(g.W / (2.0 * 3.14159265358979323846));
@@ -1289,7 +1373,9 @@ haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* 
   a.prm = nullptr;
   a.means = nullptr;
   a.counters = nullptr;
-  a.trig = nullptr;
+  a.rows = nullptr;
+  a.rtab = nullptr;
+  a.rt_stride = 0;
   a.scale = scale;
   a.u_scale = a.v_scale = 0.0f;
   // details are scaled by put(); tile means are stashed unscaled and scaled

@@ -10,11 +10,11 @@ import numpy as np
 SRC = os.path.join(os.path.dirname(__file__), "..", "paper_1705_07272_gb300", "csrc", "common.cuh")
 
 
-def _coeffs():
+def _coeffs(dtype=np.float32):
     src = open(SRC).read()
     body = src[src.index("float rot_atan2("):]
     m = re.search(r"constexpr float P\[8\] = \{([^}]*)\}", body)
-    return np.array([float(x.strip().rstrip("f")) for x in m.group(1).split(",")], dtype=np.float32)
+    return np.array([float(x.strip().rstrip("f")) for x in m.group(1).split(",")], dtype=dtype)
 
 
 def _atan2_f32(y, x, P):
@@ -56,3 +56,22 @@ def test_rotation_atan2_axes_and_origin():
     got = _atan2_f32(y, x, P)
     want = np.array([0.0, np.pi / 2, np.pi, -np.pi / 2, 0.0, np.pi / 4, -3 * np.pi / 4])
     assert np.allclose(got, want, atol=4e-7)
+
+
+def test_committed_constants_are_the_lawson_fits():
+    # the kernels' polynomials are exactly what tests/atan_fit.py derives
+    from tests.atan_fit import fit_atan_anchor, fit_atan_precise
+    assert np.allclose(_coeffs(np.float64), fit_atan_precise(), rtol=2e-9, atol=0)
+    src = open(os.path.join(os.path.dirname(SRC), "rotcoord.cuh")).read()
+    body = src[src.index("float anchor_atan2("):]
+    m = re.search(r"t \* fmaf\(([-0-9.e+]+)f, t, ([-0-9.e+]+)f\)", body)
+    got = np.array([float(m.group(2)), float(m.group(1))])
+    assert np.allclose(got, fit_atan_anchor(), rtol=2e-9, atol=0)
+
+
+def test_anchor_atan2_error_bound():
+    # the anchor arctangent only picks a pixel centre: 3.4e-3 rad is < 0.3 px at 512 columns
+    from tests.atan_fit import fit_atan_anchor
+    c0, c1 = fit_atan_anchor()
+    t = np.linspace(0.0, 1.0, 100001)
+    assert np.abs(t * (c0 + c1 * t) - np.arctan(t)).max() < 3.4e-3

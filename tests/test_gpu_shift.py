@@ -171,7 +171,7 @@ def test_rotation_matches_oracle(hs, H, W):
 
 
 def test_rotation_smooth_map_fp32_tolerance(hs):
-    # without the i.i.d. pixel noise the coordinate rounding costs far less
+    # a map of hot spots only (no per-pixel noise)
     H, W = 128, 256
     rng = np.random.default_rng(5)
     P = synth.lighting_pixels(rng, 1, H, W, sigma=0.0) - 1.0    # hot spots only
@@ -180,6 +180,22 @@ def test_rotation_smooth_map_fp32_tolerance(hs):
     got, _ = _run(hs, c, H, W, hs.HAAR_SHIFT_ROTATE_EULER, eul)
     ref = osh.haar_shift(c, H, W, osh.ROTATE_EULER, eul)
     assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("boundary", [SPH, TOR])
+def test_rotation_near_source_poles(hs, boundary):
+    # rotations that send output pixel centres onto or next to the source
+    # poles (the azimuth there is decided by float-pair products near zero):
+    # quarter and half turns about x and z, and tiny tilts
+    H, W = 64, 128
+    c = _lighting(3, H, W, 41)
+    mats = [ors.rot_x(math.pi / 2), ors.rot_z(math.pi / 2), ors.rot_x(math.pi), ors.rot_x(1e-7),
+            ors.rot_z(-1e-9) @ ors.rot_x(math.pi / 2), ors.rot_x(0.5 * math.pi / H)]
+    prm = np.stack([m.ravel() for m in mats])
+    got, _ = _run(hs, c, H, W, hs.HAAR_SHIFT_ROTATE, prm, boundary)
+    ref = osh.haar_shift(c, H, W, osh.ROTATE, prm, boundary)
+    for s in range(len(mats)):
+        assert rel_l2(got[s], ref[s]) <= ROT_TOL, (s, rel_l2(got[s], ref[s]))
 
 
 def test_rotation_about_y_equals_translation(hs):
