@@ -95,6 +95,9 @@ struct RotSrc {
   float fu, fv;    // fractions in [0, 1): the sample is at (r + fu, c + fv)
 };
 
+// GLOBAL_TABLES: colal and rows are read through the read-only data path
+// (global memory); otherwise by plain loads (e.g. tables in shared memory).
+template <bool GLOBAL_TABLES = true>
 __device__ __forceinline__ RotSrc rot_source(float4 th, float4 ab, float4 cd, float4 ps,
                                              const float4* __restrict__ colal, const float4* __restrict__ rows,
                                              float a_px, float u_scale, float v_scale, int H, int W) {
@@ -104,7 +107,7 @@ __device__ __forceinline__ RotSrc rot_source(float4 th, float4 ab, float4 cd, fl
   const fpair z2 = padd(fpair{ab.x, ab.y}, pmul(fpair{ab.z, ab.w}, cpsi));
   // azimuth: anchor column m, offset from its centre
   const int m = __float2int_rn(fmaf(anchor_atan2(x2.h, z2.h), v_scale, a_px)) & (W - 1);
-  const float4 al = __ldg(colal + m);
+  const float4 al = GLOBAL_TABLES ? __ldg(colal + m) : colal[m];
   const float cr = pdiff(x2, fpair{al.z, al.w}, z2, fpair{al.x, al.y});           // rho sin(offset)
   const fpair dt = padd(pmul(x2, fpair{al.x, al.y}), pmul(z2, fpair{al.z, al.w}));  // rho cos(offset)
   float dphi;
@@ -120,7 +123,7 @@ __device__ __forceinline__ RotSrc rot_source(float4 th, float4 ab, float4 cd, fl
   // elevation: anchor row k, offset from its centre
   int k = __float2int_rn(fmaf(anchor_atan2(rho.h, y2.h), u_scale, -0.5f));
   k = min(max(k, 0), H - 1);
-  const float4 be = __ldg(rows + k);
+  const float4 be = GLOBAL_TABLES ? __ldg(rows + k) : rows[k];
   const float sn = pdiff(rho, fpair{be.z, be.w}, y2, fpair{be.x, be.y});          // rho cos b - y2 sin b
   const float cs = fmaf(rho.h + rho.l, be.x, y2.h * be.z);                          // rho sin b + y2 cos b
   const float dth = (fabsf(sn) <= 0.0625f * cs) ? small_atan(__fdividef(sn, cs)) : rot_atan2(sn, cs);
@@ -132,6 +135,25 @@ __device__ __forceinline__ RotSrc rot_source(float4 th, float4 ab, float4 cd, fl
   o.fu = uf - fl;
   o.fv = vf - fk;
   return o;
+}
+
+// R = Ry(a) Rx(b) Ry(c) for a rotation matrix R (row-major, FP64), without
+// trigonometry: (sin a, cos a) from R's middle column, then M = Ry(-a) R =
+// Rx(b) Ry(c) gives (cos c, sin c) from its first row and (sin b, cos b) from
+// its middle column.  A positive multiple of a rotation gives the same
+// angles.  out = {sin a, cos a, sin b, cos b, sin c, cos c}.
+__device__ __forceinline__ void yxy_angles(const double R[9], double out[6]) {
+  const double na = hypot(R[1], R[7]);
+  const double sa = na > 0.0 ? R[1] / na : 0.0, ca = na > 0.0 ? R[7] / na : 1.0;
+  const double m00 = ca * R[0] - sa * R[6], m02 = ca * R[2] - sa * R[8];
+  const double m11 = R[4], m21 = sa * R[1] + ca * R[7];
+  const double nc = hypot(m00, m02), nb = hypot(m21, m11);
+  out[0] = sa;
+  out[1] = ca;
+  out[2] = nb > 0.0 ? m21 / nb : 0.0;
+  out[3] = nb > 0.0 ? m11 / nb : 1.0;
+  out[4] = nc > 0.0 ? m02 / nc : 0.0;
+  out[5] = nc > 0.0 ? m00 / nc : 1.0;
 }
 
 }  // namespace hs

@@ -1047,23 +1047,15 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
     return;
   }
   if (rot) {
-    // rotation s = blockIdx.x - nbp: R = Ry(a) Rx(b) Ry(c) (proper Euler
-    // angles), found without trigonometry: (sin a, cos a) from R's middle
-    // column, then M = Ry(-a) R = Rx(b) Ry(c) gives (cos c, sin c) from its
-    // first row and (sin b, cos b) from its middle column
+    // rotation s = blockIdx.x - nbp: R = Ry(a) Rx(b) Ry(c) (proper Euler angles)
     const int s = blockIdx.x - a.nbp;
     __shared__ double sh[6];
     if (threadIdx.x == 0) {
-      double R[9];
+      double R[9], ang[6];
       rotation_matrix(a, s, R);
-      const double na = hypot(R[1], R[7]);
-      const double sa = na > 0.0 ? R[1] / na : 0.0, ca = na > 0.0 ? R[7] / na : 1.0;
-      const double m00 = ca * R[0] - sa * R[6], m02 = ca * R[2] - sa * R[8];
-      const double m11 = R[4], m21 = sa * R[1] + ca * R[7];
-      const double nc = hypot(m00, m02), nb = hypot(m21, m11);
-      sh[0] = sa; sh[1] = ca;
-      sh[2] = nb > 0.0 ? m21 / nb : 0.0; sh[3] = nb > 0.0 ? m11 / nb : 1.0;
-      sh[4] = nc > 0.0 ? m02 / nc : 0.0; sh[5] = nc > 0.0 ? m00 / nc : 1.0;
+      yxy_angles(R, ang);
+      for (int k = 0; k < 6; ++k) sh[k] = ang[k];
+      const double sa = ang[0], ca = ang[1];
       ShiftParam p;
       p.kx = p.ky = 0;
       p.wx0 = p.wy0 = 1.0f;

@@ -13,6 +13,7 @@
 // parent's plus the parent's three details times their +-1/B signs.
 #include <math.h>
 
+#include "rotcoord.cuh"
 #include "tc.cuh"
 
 namespace hs {
@@ -216,15 +217,15 @@ __global__ void __launch_bounds__(T) k_triple(TripleArgs a) {
 struct ShadeTripleArgs {
   TripleArgs t;
   const float* F;            // [H][W] the local BRDF map in pixels
-  const float2* tab_t;       // [H] (sin, cos) of theta_i
-  const float2* tab_p;       // [W] (sin, cos) of phi_j
+  const float4* tab_t;       // [H] (sin, cos) of theta_i as float pairs (hi, lo, hi, lo)
+  const float4* tab_p;       // [W] (sin, cos) of phi_j as float pairs
   const double* params;      // [V][9] rotation records
 };
 
 // Set-up: blocks 0..C-1 the lighting means, block C the BRDF's pixel map
 // (inverse transform, top down in shared memory) and the angle tables.
 __global__ void __launch_bounds__(256) k_shade_triple_setup(ShadeTripleArgs s, const float* brdf_local, float* F,
-                                                           float2* tab_t, float2* tab_p) {
+                                                           float4* tab_t, float4* tab_p) {
   const TripleArgs& a = s.t;
   if (blockIdx.x < (unsigned)gridDim.x - 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.status = 0;
@@ -256,40 +257,71 @@ __global__ void __launch_bounds__(256) k_shade_triple_setup(ShadeTripleArgs s, c
   for (int i = threadIdx.x; i < a.H; i += blockDim.x) {
     double sv, cv;
     sincospi((i + 0.5) / a.H, &sv, &cv);
-    tab_t[i] = make_float2((float)sv, (float)cv);
+    const float sh = (float)sv, ch = (float)cv;
+    tab_t[i] = make_float4(sh, (float)(sv - (double)sh), ch, (float)(cv - (double)ch));
   }
   for (int j = threadIdx.x; j < a.W; j += blockDim.x) {
     double sv, cv;
     sincospi(2.0 * (j + 0.5) / a.W, &sv, &cv);
-    tab_p[j] = make_float2((float)sv, (float)cv);
+    const float sh = (float)sv, ch = (float)cv;
+    tab_p[j] = make_float4(sh, (float)(sv - (double)sh), ch, (float)(cv - (double)ch));
   }
 }
 
-// The rotated BRDF at output pixel (i, j): q = R p(theta_i, phi_j), source
-// position (Theta / dtheta - 1/2, Phi / dphi - 1/2), bilinear with the SPHERE
-// extension (one reflection across a pole at most: u in [-1/2, H - 1/2]).
-__device__ __forceinline__ float rot_sample(const ShadeTripleArgs& s, const float (&R)[9], int i, int j,
+// Per-vertex rotation tables in shared memory for rot_source (R = Ry(a)
+// Rx(b) Ry(c) of the vertex's record): sin/cos(phi_j + c) [W], sin/cos(phi_m
+// - a) [W] and the row products of b [2H], all float pairs, built from the
+// map's FP64-derived pair tables and the record's angles by error-free
+// products and sums.
+struct RotTabs {
+  float4* psi;
+  float4* al;
+  float4* row;
+  float a_px;
+};
+
+__device__ __forceinline__ fpair fp_split(double x) {
+  const float h = (float)x;
+  return fpair{h, (float)(x - (double)h)};
+}
+
+__device__ void build_rot_tabs(const ShadeTripleArgs& s, const double* ang, const RotTabs& rt, int t, int T) {
+  const TripleArgs& a = s.t;
+  const fpair sa = fp_split(ang[0]), ca = fp_split(ang[1]), sb = fp_split(ang[2]), cb = fp_split(ang[3]);
+  const fpair sc = fp_split(ang[4]), cc = fp_split(ang[5]);
+  for (int j = t; j < a.W; j += T) {
+    const float4 p = s.tab_p[j];
+    const fpair sp{p.x, p.y}, cp{p.z, p.w};
+    const fpair s1 = padd(pmul(sp, cc), pmul(cp, sc)), c1 = padd(pmul(cp, cc), pneg(pmul(sp, sc)));
+    const fpair s2 = padd(pmul(sp, ca), pneg(pmul(cp, sa))), c2 = padd(pmul(cp, ca), pmul(sp, sa));
+    rt.psi[j] = make_float4(s1.h, s1.l, c1.h, c1.l);
+    rt.al[j] = make_float4(s2.h, s2.l, c2.h, c2.l);
+  }
+  for (int i = t; i < a.H; i += T) {
+    const float4 q = s.tab_t[i];
+    const fpair st{q.x, q.y}, ct{q.z, q.w};
+    const fpair A = pmul(sb, ct), B = pmul(cb, st), C = pmul(cb, ct), D = pmul(sb, st);
+    rt.row[2 * i] = make_float4(A.h, A.l, B.h, B.l);
+    rt.row[2 * i + 1] = make_float4(C.h, C.l, D.h, D.l);
+  }
+}
+
+// The rotated BRDF at output pixel (i, j): the source position from
+// rot_source (integer anchors plus float-pair offsets), bilinear with the
+// SPHERE extension (one reflection across a pole at most).
+__device__ __forceinline__ float rot_sample(const ShadeTripleArgs& s, const RotTabs& rt, int i, int j,
                                             float inv_dth, float inv_dph) {
   const TripleArgs& a = s.t;
-  const float2 th = s.tab_t[i], ph = s.tab_p[j];
-  const float p0 = th.x * ph.x, p1 = th.y, p2 = th.x * ph.y;
-  const float qx = R[0] * p0 + R[1] * p1 + R[2] * p2;
-  const float qy = R[3] * p0 + R[4] * p1 + R[5] * p2;
-  const float qz = R[6] * p0 + R[7] * p1 + R[8] * p2;
-  const float u = fmaf(rot_atan2(sqrtf(qx * qx + qz * qz), qy), inv_dth, -0.5f);
-  const float w = fmaf(rot_atan2(qx, qz), inv_dph, -0.5f);
-  const float fi = floorf(u), fj = floorf(w);
-  const float fu = u - fi, fv = w - fj;
-  const int i0 = (int)fi, j0 = (int)fj;
-  int r0 = i0, r1 = i0 + 1, s0 = 0, s1 = 0;
-  if (r0 < 0) { r0 = -1 - r0; s0 = a.W >> 1; }
-  if (r1 >= a.H) { r1 = 2 * a.H - 1 - r1; s1 = a.W >> 1; }
-  r0 = min(max(r0, 0), a.H - 1);                   // only a non-finite record gets clamped
-  r1 = min(max(r1, 0), a.H - 1);
+  const RotSrc o = rot_source<false>(s.tab_t[i], rt.row[2 * i], rt.row[2 * i + 1], rt.psi[j], rt.al, s.tab_t,
+                                     rt.a_px, inv_dth, inv_dph, a.H, a.W);
+  int r0 = o.r, r1 = o.r + 1, s0 = 0, s1 = 0;
+  if (r0 < 0) { r0 = 0; s0 = a.W >> 1; }
+  if (r1 >= a.H) { r1 = a.H - 1; s1 = a.W >> 1; }
   const int m = a.W - 1;
-  const float f00 = __ldg(s.F + r0 * a.W + ((j0 + s0) & m)), f01 = __ldg(s.F + r0 * a.W + ((j0 + 1 + s0) & m));
-  const float f10 = __ldg(s.F + r1 * a.W + ((j0 + s1) & m)), f11 = __ldg(s.F + r1 * a.W + ((j0 + 1 + s1) & m));
-  return (1.0f - fu) * ((1.0f - fv) * f00 + fv * f01) + fu * ((1.0f - fv) * f10 + fv * f11);
+  const float f00 = __ldg(s.F + r0 * a.W + ((o.c + s0) & m)), f01 = __ldg(s.F + r0 * a.W + ((o.c + 1 + s0) & m));
+  const float f10 = __ldg(s.F + r1 * a.W + ((o.c + s1) & m)), f11 = __ldg(s.F + r1 * a.W + ((o.c + 1 + s1) & m));
+  const float top = fmaf(o.fv, f01 - f00, f00), bot = fmaf(o.fv, f11 - f10, f10);
+  return fmaf(o.fu, bot - top, top);
 }
 
 template <int C, int T>
@@ -299,6 +331,11 @@ __global__ void __launch_bounds__(T) k_shade_triple(ShadeTripleArgs s) {
   float* sc = sm;                      // [N] visibility row
   float* mc = sc + a.N;                // [Nm] visibility means, level n first
   float* sa = mc + a.Nm;               // [Nm] the rotated BRDF's scaling values A_l, same layout
+  RotTabs rt;                          // [2W + 2H] float4 after them, 16-byte aligned
+  rt.psi = reinterpret_cast<float4*>(sm + ((a.N + 2 * a.Nm + 3) & ~3));
+  rt.al = rt.psi + a.W;
+  rt.row = rt.al + a.W;
+  __shared__ double ang[6];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ int abort_flag;
   __shared__ float red[T / 32][C];
@@ -314,9 +351,14 @@ __global__ void __launch_bounds__(T) k_shade_triple(ShadeTripleArgs s) {
     tc::mbar_arrive_tx(b32, (uint32_t)a.N * 4u);
     bulk_g2s(tc::smem_u32(sc), a.vis + (long long)v * a.sv, (uint32_t)a.N * 4u, b32);
   }
-  float R[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) R[k] = (float)s.params[9 * (long long)v + k];
+  if (t == 0) {
+    double R[9];
+    for (int k = 0; k < 9; ++k) R[k] = s.params[9 * (long long)v + k];
+    yxy_angles(R, ang);
+  }
+  __syncthreads();
+  rt.a_px = (float)(atan2(ang[0], ang[1]) * (a.W / (2.0 * 3.14159265358979323846)) - 0.5);
+  build_rot_tabs(s, ang, rt, t, T);
   const int logW = 31 - __clz(a.W);
   const float inv_dth = (float)a.H * 0.318309886183791f, inv_dph = (float)a.W * 0.159154943091895f;
   bool ok = true;
@@ -350,10 +392,10 @@ __global__ void __launch_bounds__(T) k_shade_triple(ShadeTripleArgs s) {
       const int r = k >> lc, col = k & (cols - 1);
       float ta, tb, tc_, td;
       if (l == 1) {
-        ta = rot_sample(s, R, 2 * r, 2 * col, inv_dth, inv_dph);
-        tb = rot_sample(s, R, 2 * r, 2 * col + 1, inv_dth, inv_dph);
-        tc_ = rot_sample(s, R, 2 * r + 1, 2 * col, inv_dth, inv_dph);
-        td = rot_sample(s, R, 2 * r + 1, 2 * col + 1, inv_dth, inv_dph);
+        ta = rot_sample(s, rt, 2 * r, 2 * col, inv_dth, inv_dph);
+        tb = rot_sample(s, rt, 2 * r, 2 * col + 1, inv_dth, inv_dph);
+        tc_ = rot_sample(s, rt, 2 * r + 1, 2 * col, inv_dth, inv_dph);
+        td = rot_sample(s, rt, 2 * r + 1, 2 * col + 1, inv_dth, inv_dph);
       } else {
         const float* c0 = src + (2 * r) * (2 * cols) + 2 * col;
         ta = c0[0];
@@ -404,12 +446,12 @@ static long long round4(long long x) { return (x + 3) & ~3LL; }
 
 long long shade_triple_work_floats(int H, int W, int C) {
   const long long N = (long long)H * W, q = W / H, Nm = (N - q) / 3;
-  return 4 + round4((long long)C * Nm) + 4LL * C * Nm + round4(N) + 2LL * H + 2LL * W;
+  return 4 + round4((long long)C * Nm) + 4LL * C * Nm + round4(N) + 4LL * H + 4LL * W;
 }
 
 template <int C>
 static haar_status_t launch_shade_triple_c(const ShadeTripleArgs& s, const float* brdf_local, float* F,
-                                           float2* tab_t, float2* tab_p, cudaStream_t st) {
+                                           float4* tab_t, float4* tab_p, cudaStream_t st) {
   const TripleArgs& a = s.t;
   const size_t setup_smem = 2 * (size_t)a.N * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_shade_triple_setup, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -418,7 +460,7 @@ static haar_status_t launch_shade_triple_c(const ShadeTripleArgs& s, const float
   k_shade_triple_setup<<<C + 1, 256, setup_smem, st>>>(s, brdf_local, F, tab_t, tab_p);
   haar_status_t r = cuda_check(cudaGetLastError(), "k_shade_triple_setup launch");
   if (r != HAAR_OK) return r;
-  const size_t smem = ((size_t)a.N + 2 * (size_t)a.Nm) * sizeof(float);
+  const size_t smem = ((((size_t)a.N + 2 * (size_t)a.Nm + 3) & ~(size_t)3) + 8 * ((size_t)a.W + a.H)) * sizeof(float);
   if (a.N <= 2048) {
     e = cudaFuncSetAttribute(k_shade_triple<C, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "k_shade_triple attribute");
@@ -461,8 +503,8 @@ haar_status_t launch_shade_triple(int H, int W, int C, int V, const float* light
   float4* pk = reinterpret_cast<float4*>(ma + round4((long long)C * a.Nm));
   a.pk = pk;
   float* F = reinterpret_cast<float*>(pk + (long long)C * a.Nm);
-  float2* tab_t = reinterpret_cast<float2*>(F + round4(a.N));
-  float2* tab_p = tab_t + H;
+  float4* tab_t = reinterpret_cast<float4*>(F + round4(a.N));
+  float4* tab_p = tab_t + H;
   s.F = F;
   s.tab_t = tab_t;
   s.tab_p = tab_p;
