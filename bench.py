@@ -45,68 +45,330 @@ def parse():
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements of the other configs")
     ap.add_argument("--only", default=None,
                     help="comma-separated rows to run alone (no c1 frame), for profiling one kernel")
-    ap.add_argument("--cpu-sample", type=int, default=2000, help="vertices in the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=128,
+                    help="vertices per host process in the oracle's timed frame sample")
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------- oracle timing
 
-def oracle_frame_sample(n_vertices: int, seed_stream: int = 0):
-    """Time the CPU oracle on one c1 frame: the full 16-shift phase shift and
-    the brute-force double product of a sample of vertices.  Returns
-    (seconds for the shift, seconds per vertex of shading, vertices)."""
+def _oracle_worker(conn, cid, verts, shm_name, shape):
+    """One host process of the oracle's timed frame.  Before timing it builds
+    the stored top-256 transport of its vertices (oracle projection); then, on
+    command, it computes oracle shifts into the shared lighting buffer or
+    shades its vertices from that buffer (brute force through pixel space)."""
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
     import numpy as np
+    import torch
+    from multiprocessing import shared_memory
+    torch.set_num_threads(1)
     import synth
     from oracle import haar, shade, shift, transport
-    sc = synth.scene(1, V=n_vertices)
+    sc = synth.scene(cid)
     H, W = sc["H"], sc["W"]
-    w = synth.transport_weights(sc["pos"], sc["nrm"], sc["occ_c"], sc["occ_r"], H, W).numpy()
-    T = transport.project(w)
-    vals, idx, rowptr = transport.topk_csr(T, 256)
-    dense = transport.csr_dense(vals, idx, rowptr, H * W)
     L = haar.forward(sc["light"])
-    t0 = time.perf_counter()
-    Ls = shift.haar_shift(L, H, W, shift.TRANSLATE, sc["params"])
-    t1 = time.perf_counter()
-    shade.radiance(Ls, dense, H, W)
-    t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / n_vertices, n_vertices
+    T = None
+    if len(verts):
+        w = synth.transport_weights(sc["pos"][verts], sc["nrm"][verts], sc["occ_c"], sc["occ_r"], H, W).numpy()
+        vals, idx, rowptr = transport.topk_csr(transport.project(w), 256)
+        T = transport.csr_dense(vals, idx, rowptr, H * W)
+        del w
+    shm = shared_memory.SharedMemory(name=shm_name)
+    Ls = np.ndarray(shape, dtype=np.float64, buffer=shm.buf)
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg[0] == "shift":
+            for s in msg[1]:
+                Ls[s] = shift.haar_shift(L, H, W, shift.TRANSLATE, sc["params"][s:s + 1])[0]
+            conn.send("done")
+        elif msg[0] == "shade":
+            r = shade.radiance(Ls, T, H, W) if T is not None else np.zeros((0, shape[0], shape[1]))
+            conn.send(r.shape[0])
+        else:
+            break
+    del Ls
+    shm.close()
 
 
-def cpu_baseline(sample: int):
-    t_shift, t_vert, n = oracle_frame_sample(sample)
-    V, S = 50000, 16
-    frame = t_shift + t_vert * V
-    return {"value": V * S / frame / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one frame's 16-shift phase shift (full map) + brute-force pixel-space shading of "
-                      f"{n} of the 50000 vertices, scaled to the frame: shift {t_shift:.2f} s, "
-                      f"{t_vert * 1e3:.2f} ms per vertex (numpy FP64, single process)"}
+class OracleFrame:
+    """The CPU FP64 oracle (unmodified) on a bounded sample of the headline
+    frame, spread over `procs` host processes: a step is the frame's 16-shift
+    phase shift of the full RGB 128x256 map (shifts divided among the
+    processes) followed by the brute-force shading of `n` of its vertices
+    (evenly spaced over the 50 000; divided among the processes).  Each
+    process is single-threaded; the pool is started with `spawn`."""
+
+    def __init__(self, procs: int, n: int):
+        import multiprocessing as mp
+        import numpy as np
+        from multiprocessing import shared_memory
+        import synth
+        self.procs, self.n = procs, n
+        wl = synth.WORKLOADS[1]
+        self.S = wl.S
+        shape = (wl.S, wl.C, wl.H * wl.W)
+        self.shm = shared_memory.SharedMemory(create=True, size=int(np.prod(shape)) * 8)
+        verts = np.linspace(0, wl.V - 1, n).astype(np.int64)
+        ctx = mp.get_context("spawn")
+        self.conns, self.workers = [], []
+        for k, part in enumerate(np.array_split(verts, procs)):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, 1, part, self.shm.name, shape), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.workers.append(pr)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def step(self) -> float:
+        """Seconds of one frame sample (wall clock)."""
+        t0 = time.perf_counter()
+        for k, c in enumerate(self.conns):
+            c.send(("shift", list(range(k, self.S, self.procs))))
+        for c in self.conns:
+            c.recv()
+        for c in self.conns:
+            c.send(("shade",))
+        done = sum(c.recv() for c in self.conns)
+        assert done == self.n
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            c.send(("stop",))
+        for w in self.workers:
+            w.join(timeout=30)
+        self.shm.close()
+        self.shm.unlink()
+
+    def sample_text(self) -> str:
+        return (f"each step: the frame's 16-shift phase shift of the full RGB 128x256 map and the brute-force "
+                f"pixel-space shading of {self.n} of its 50000 vertices (evenly spaced), numpy FP64 oracle in "
+                f"{self.procs} single-threaded host processes; value = {self.n} x 16 vertex-rotations / measured "
+                f"step time")
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(per_proc: int):
+    """The oracle on all host cores (2 timed steps after one warm-up) and in
+    one process, each on a bounded sample of the frame."""
+    P = host_cores()
+    fr = OracleFrame(P, P * per_proc)
+    fr.step()
+    t = statistics.mean(fr.step() for _ in range(2))
+    out = {"value": fr.n * 16 / t / 1e6, "unit": UNIT, "cores": P, "kind": "oracle", "step_s": t,
+           "sample": fr.sample_text()}
+    fr.close()
+    one = OracleFrame(1, per_proc)
+    t1 = one.step()
+    out["single_thread"] = {"value": one.n * 16 / t1 / 1e6, "unit": UNIT, "cores": 1, "step_s": t1,
+                            "sample": one.sample_text()}
+    one.close()
+    return out
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    per_step_vertices = max(50, args.cpu_sample // 10)
+    P = host_cores()
+    fr = OracleFrame(P, P * args.cpu_sample)
     times = []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        t_shift, t_vert, n = oracle_frame_sample(per_step_vertices)
-        dt = t_shift + t_vert * 50000
+        dt = fr.step()
         if i >= args.warmup:
             times.append(dt)
-    frame = statistics.mean(times)
-    value = 50000 * 16 / frame / 1e6
+    fr.close()
+    step_s = statistics.mean(times)
+    value = fr.n * 16 / step_s / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the full 16-shift phase shift + brute-force shading of "
-                                       f"{per_step_vertices} vertices, scaled to the 50000-vertex frame"},
+            "data": "synthetic", "config": bench_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+                             "sample": fr.sample_text()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_config(world: int = 1):
+    return {"workload": WORKLOAD, "H": 128, "W": 256, "channels": 3, "shifts_per_step": 16,
+            "vertices_per_gpu": 50000, "topk": 256, "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"{world} independent vertex shards (no collective)"}
+
+
+# ----------------------------------------------------------------- oracle checks
+
+CHECK_VERTS = {"c1": 48, "c2": 64, "c3": 24}
+
+
+def oracle_checks():
+    """Sampled FP64-oracle results for the bench rows, computed on the host
+    (the CPU-baseline leg) before any GPU work.  Every input is built by the
+    oracle from the seeded scenes (lighting coefficients, stored transports,
+    view bins); the GPU side re-runs each row's launches on these inputs and
+    states the relative L2 error of the sampled outputs."""
+    import numpy as np
+    import synth
+    from oracle import haar, shade, shift, transport
+    f32 = lambda x: np.asarray(x, dtype=np.float32).astype(np.float64)
+    out = {}
+
+    def weights(sc, vs, Ht, Wt, **kw):
+        return synth.transport_weights(sc["pos"][vs], sc["nrm"][vs], sc["occ_c"], sc["occ_r"], Ht, Wt,
+                                       **kw).numpy()
+
+    # c0: the whole frame (1 shift of the 32x32 map, 1000 vertices, dense FP32)
+    sc = synth.scene(0)
+    L = f32(haar.forward(sc["light"]))
+    T = f32(transport.project(weights(sc, slice(None), 32, 32)))
+    ref = shade.radiance(shift.haar_shift(L, 32, 32, shift.TRANSLATE, sc["params"]), T, 32, 32)
+    out["c0"] = dict(L=L, T=T, params=sc["params"], ref=ref)
+    # c1: the frame's 16 shifts; shading of evenly spaced vertices (top-256 FP32 CSR)
+    sc = synth.scene(1)
+    H, W, N = sc["H"], sc["W"], sc["H"] * sc["W"]
+    L1 = f32(haar.forward(sc["light"]))
+    vs = np.linspace(0, sc["V"] - 1, CHECK_VERTS["c1"]).astype(np.int64)
+    vals, idx, rowptr = transport.topk_csr(transport.project(weights(sc, vs, H, W)), 256)
+    vals = f32(vals)
+    Ls = shift.haar_shift(L1, H, W, shift.TRANSLATE, sc["params"])
+    out["c1"] = dict(L=L1, vals=vals, idx=idx, rowptr=rowptr, params=sc["params"], lighting=Ls,
+                     ref=shade.radiance(Ls, transport.csr_dense(vals, idx, rowptr, N), H, W))
+    # translation batch: sampled shifts of the 4096
+    prm = synth.translations(synth.rng_for(1, 7), 4096, 256.0, 256.0)
+    smp = [0, 2048, 4095]
+    out["translation_shift_batch"] = dict(L=L1, params=prm, sample=smp,
+                                          ref=shift.haar_shift(L1, H, W, shift.TRANSLATE, prm[smp]))
+    # rotation batch: sampled rotations of the 512
+    sc2 = synth.scene(2)
+    L2 = f32(haar.forward(sc2["light"]))
+    eul = synth.euler_angles(synth.rng_for(2, 7), 512)
+    smp = [0, 511]
+    out["rotation_shift_batch"] = dict(L=L2, params=eul, sample=smp,
+                                       ref=shift.haar_shift(L2, 256, 512, shift.ROTATE_EULER, eul[smp]))
+    # c2: the 64 rotations (bf16 hi + lo of the lowest 4096), sampled vertices and rotations;
+    # stored transport = the lowest 4096 coefficients in bf16
+    vs = np.linspace(0, sc2["V"] - 1, CHECK_VERTS["c2"]).astype(np.int64)
+    Tb = transport.to_bf16(transport.project(weights(sc2, vs, 64, 128), 256, 512)[:, :4096])
+    smp = [0, 21, 42, 63]
+    Ls = shift.haar_shift(L2, 256, 512, shift.ROTATE_EULER, sc2["params"][smp], out_coeffs=4096)
+    out["c2_dense_tc"] = dict(L=L2, T=Tb, params=sc2["params"], sample=smp,
+                              ref=shade.radiance(Ls, Tb, 256, 512))
+    # c3: view bins of sampled vertices for the 32 cameras, 16 bins x top-512 FP16 glossy transport,
+    # sampled (rotation, view) pairs
+    sc3 = synth.scene(3)
+    L3 = f32(haar.forward(sc3["light"]))
+    nv = CHECK_VERTS["c3"]
+    vs = np.linspace(0, sc3["V"] - 1, nv).astype(np.int64)
+    dirs = synth.view_bin_dirs(16)
+    view = synth.bin_view_world(sc3["nrm"][vs], 16).reshape(-1, 3)
+    rep = np.repeat(vs, 16)
+    w = synth.transport_weights(sc3["pos"][rep], sc3["nrm"][rep], sc3["occ_c"], sc3["occ_r"], 64, 128,
+                                view=view, expo=sc3["expo"][rep]).numpy()
+    vals, idx, _ = transport.topk_csr(transport.project(w, 256, 512)[:, :8192], 512)
+    vals = transport.to_f16(vals).reshape(nv, 16, 512)
+    idx = idx.reshape(nv, 16, 512)
+    pos, nrm, cams = f32(sc3["pos"][vs]), f32(sc3["nrm"][vs]), f32(sc3["cams"])
+    bins, margin = transport.view_bins(pos, nrm, cams, f32(dirs))
+    smp = [0, 11, 22, 31]
+    Ls = shift.haar_shift(L3, 256, 512, shift.ROTATE_EULER, sc3["params"][smp])
+    ref = np.zeros((nv, len(smp), 3))
+    for k, s in enumerate(smp):
+        for v in range(nv):
+            Tv = np.zeros((1, 256 * 512))
+            Tv[0, idx[v, bins[s, v]]] = vals[v, bins[s, v]]
+            ref[v, k] = shade.radiance(Ls[k:k + 1], Tv, 256, 512)[0, 0]
+    out["c3_bincsr"] = dict(L=L3, vals=vals, idx=idx, pos=pos, nrm=nrm, cams=cams, dirs=dirs, bins=bins,
+                            margin=margin, params=sc3["params"], sample=smp, ref=ref)
+    return out
+
+
+def _rel(a, b):
+    import numpy as np
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_checks(hs, dev, chk):
+    """The rows' launches on the oracle's inputs; relative L2 error of the
+    sampled outputs against the oracle (max over the sampled shifts or
+    rotations where there are several)."""
+    import numpy as np
+    import torch
+    t = lambda x, dt=torch.float32: torch.tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    res = {}
+    c = chk["c0"]
+    plan = hs.Plan(32, 32, 1, max_shifts=1)
+    tr = hs.Transport(hs.HAAR_T_DENSE_F32, c["T"].shape[0], c["T"].shape[1], t(c["T"]))
+    R = hs.shade_batch(plan, t(c["L"]), t(c["params"], torch.float64), tr).cpu().numpy()
+    res["c0"] = {"rel_l2_vs_oracle": _rel(R, c["ref"]), "checked": "the whole frame (1000 vertices)"}
+    plan.close()
+
+    c = chk["c1"]
+    plan = hs.Plan(128, 256, 3, max_shifts=16, out_layout=hs.HAAR_LAYOUT_KSC)
+    lit = hs.haar_shift(plan, t(c["L"]), t(c["params"], torch.float64))
+    V = len(c["rowptr"]) - 1
+    g = hs.haar_transport_group(V, 128 * 256, t(c["rowptr"], torch.int32), t(c["idx"].astype(np.int16), torch.int16),
+                                t(c["vals"]))
+    R = hs.shade_vertices(plan, g, lit, 16).cpu().numpy()
+    lk = lit.double().cpu().numpy().transpose(1, 2, 0)                     # KSC -> [S][C][K]
+    res["c1"] = {"rel_l2_vs_oracle": _rel(R, c["ref"]), "shift_rel_l2_vs_oracle": _rel(lk, c["lighting"]),
+                 "checked": f"the frame's 16 shifts (all coefficients) and the shading of {V} of the 50000 vertices"}
+    plan.close()
+
+    for name, H, W, kind in (("translation_shift_batch", 128, 256, hs.HAAR_SHIFT_TRANSLATE),
+                             ("rotation_shift_batch", 256, 512, hs.HAAR_SHIFT_ROTATE_EULER)):
+        c = chk[name]
+        S = len(c["params"])
+        plan = hs.Plan(H, W, 3, kind=kind, max_shifts=S)
+        o = hs.haar_shift(plan, t(c["L"]), t(c["params"], torch.float64))
+        got = o[torch.tensor(c["sample"], device=dev)].double().cpu().numpy()
+        res[name] = {"rel_l2_vs_oracle": max(_rel(got[k], c["ref"][k]) for k in range(len(c["sample"]))),
+                     "checked": f"shifts {c['sample']} of the {S}-shift launch"}
+        plan.close()
+        del o
+
+    c = chk["c2_dense_tc"]
+    plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=64, out_coeffs=4096,
+                   out_type=hs.HAAR_OUT_BF16_HILO)
+    lit = hs.haar_shift(plan, t(c["L"]), t(c["params"], torch.float64))
+    V = c["T"].shape[0]
+    tr = hs.Transport(hs.HAAR_T_DENSE_BF16, V, 4096, t(c["T"], torch.bfloat16))
+    R = hs.shade_vertices(plan, tr, lit, 64)[:, c["sample"]].cpu().numpy()
+    res["c2_dense_tc"] = {"rel_l2_vs_oracle": max(_rel(R[:, k], c["ref"][:, k]) for k in range(len(c["sample"]))),
+                          "checked": f"rotations {c['sample']} of the 64 (bf16 hi + lo lighting) for {V} of the "
+                                     f"200000 vertices; error of the hi/lo lighting and the tensor-core "
+                                     f"accumulation against the FP64 double product of the stored bf16 transport"}
+    plan.close()
+
+    c = chk["c3_bincsr"]
+    plan = hs.Plan(256, 512, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=32, out_layout=hs.HAAR_LAYOUT_SKC4)
+    lit = hs.haar_shift(plan, t(c["L"]), t(c["params"], torch.float64))
+    bins = hs.haar_view_bins(t(c["pos"]), t(c["nrm"]), t(c["cams"]), t(c["dirs"]))
+    b = bins.cpu().numpy().astype(np.int64)
+    ok = c["margin"] > 1e-5
+    V = c["vals"].shape[0]
+    tr = hs.Transport(hs.HAAR_T_BINCSR_F16_U32, V, 512, t(c["vals"], torch.float16),
+                      t(c["idx"].astype(np.int32), torch.int32), bins=16, bin_of=bins)
+    R = hs.shade_vertices(plan, tr, lit, 32)[:, c["sample"]].cpu().numpy()
+    okp = ok[c["sample"]].T
+    res["c3_bincsr"] = {"rel_l2_vs_oracle": max(_rel(R[:, k][okp[:, k]], c["ref"][:, k][okp[:, k]])
+                                                for k in range(len(c["sample"]))),
+                        "view_bins_equal": bool(np.array_equal(b[ok], c["bins"][ok])),
+                        "checked": f"pairs {c['sample']} of the 32 for {V} of the 100000 vertices (view bins away "
+                                   f"from near-ties); FP16 transport summed in FP32"}
+    plan.close()
+    return res
 
 
 # ----------------------------------------------------------------- GPU workload
@@ -216,10 +478,11 @@ def _bf16_peak():
     return d.get("bf16_tflops", 1900.0), d.get("hbm_gbs", 6800.0)
 
 
-def _glossy_transport(hs, sc, dev, bins=16, K=512, chunk=8192):
+def _glossy_transport(hs, sc, dev, bins=16, K=512, chunk=8192, expo=None, by_magnitude=False):
     """View-binned top-K glossy transport of every (vertex, bin) on the GPU:
     Phong transfer on the 64x128 grid, projected by haar_forward (the lowest
-    8192 coefficients of the 256x512 map), top-K per row, sorted by index."""
+    8192 coefficients of the 256x512 map), top-K per row, sorted by index (or
+    by decreasing magnitude); `expo` overrides every vertex's Phong exponent."""
     import numpy as np
     import torch
     import synth
@@ -232,17 +495,112 @@ def _glossy_transport(hs, sc, dev, bins=16, K=512, chunk=8192):
     for a in range(0, rows, chunk):
         b = min(rows, a + chunk)
         vi = np.arange(a, b) // bins
+        ex = sc["expo"][vi] if expo is None else np.full(b - a, float(expo))
         w = synth.transport_weights(sc["pos"][vi], sc["nrm"][vi], sc["occ_c"], sc["occ_r"], 64, 128,
-                                    view=view[a:b], expo=sc["expo"][vi], device=dev, dtype=torch.float32,
+                                    view=view[a:b], expo=ex, device=dev, dtype=torch.float32,
                                     chunk=chunk)
         T = hs.haar_forward(w.contiguous(), scale=0.25)
         absum += T.abs().sum(0).double()
-        top = torch.topk(T.abs(), K, dim=1).indices
-        top, _ = torch.sort(top, dim=1)
+        top = torch.topk(T.abs(), K, dim=1, sorted=by_magnitude).indices
+        if not by_magnitude:
+            top, _ = torch.sort(top, dim=1)
         idx[a:b] = top.to(torch.int32)
         vals[a:b] = torch.gather(T, 1, top).to(torch.float16)
         del w, T
     return vals.reshape(V, bins, K), idx.reshape(V, bins, K), absum
+
+
+def _init_params(rng):
+    """He-initialised weights, zero biases, in the flat order haar_mlp_set_params takes."""
+    import numpy as np
+    flat = []
+    for fi, fo in ((320, 256), (256, 256), (256, 256), (256, 256), (256, 512)):
+        flat += [rng.standard_normal(fo * fi) * math.sqrt(2.0 / fi), np.zeros(fo)]
+    return np.concatenate(flat)
+
+
+def _glossy_pairs(rng, sc, n):
+    """n random (vertex, camera) pairs of the glossy scene: the surrogate's
+    raw inputs [n, 9] (position, normal, view direction) and the transfer
+    parameters of each pair."""
+    import numpy as np
+    import synth
+    vid = rng.integers(0, sc["V"], n)
+    cams = synth.cameras(rng, n)
+    pos, nrm, expo = sc["pos"][vid], sc["nrm"][vid], sc["expo"][vid]
+    view = cams - pos
+    view /= np.linalg.norm(view, axis=1, keepdims=True)
+    raw = np.concatenate([pos, nrm, view], axis=1).astype(np.float32)
+    return raw, (pos, nrm, view, expo)
+
+
+def _glossy_rows(hs, sc, dev, gen, fn, chunk=8192):
+    """The lowest 8192 coefficients of every pair's transport (Phong transfer
+    on the 64x128 grid, projected by haar_forward; finer levels of the
+    256x512 map are zero), handed to fn(a, b, T[b - a, 8192]) chunk by chunk."""
+    import torch
+    import synth
+    pos, nrm, view, expo = gen
+    n = len(pos)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        w = synth.transport_weights(pos[a:b], nrm[a:b], sc["occ_c"], sc["occ_r"], 64, 128, view=view[a:b],
+                                    expo=expo[a:b], device=dev, dtype=torch.float32, chunk=chunk)
+        fn(a, b, hs.haar_forward(w.contiguous(), scale=0.25))
+        del w
+
+
+def _surrogate_accuracy(hs, net, sc, dev, lit, bins, vals, idx, isel, mu, sg, absum, n_eval=8192):
+    """Radiance of sampled (vertex, pair) of the c4 frame from (a) the trained
+    surrogate, (b) the view-binned stored transport of the c3 frame (the plain
+    method), (c) the transport at the exact view, untruncated, and (d) that
+    transport restricted to the surrogate's index set; relative L2 errors, and
+    the index-set truncation error for larger index sets."""
+    import numpy as np
+    import torch
+    V, S = sc["V"], sc["S"]
+    rng = np.random.default_rng(43)
+    vid = rng.integers(0, V, n_eval)
+    sid = rng.integers(0, S, n_eval)
+    pos, nrm, expo = sc["pos"][vid], sc["nrm"][vid], sc["expo"][vid]
+    view = sc["cams"][sid] - pos
+    view /= np.linalg.norm(view, axis=1, keepdims=True)
+    raw = torch.tensor(np.concatenate([pos, nrm, view], axis=1), dtype=torch.float32, device=dev)
+    Lk = lit.reshape(S, -1, 4)[:, :8192, :3].double()                   # SKC4 -> [S][8192][3]
+    s_t = torch.tensor(sid, device=dev)
+    v_t = torch.tensor(vid, device=dev)
+    Te = torch.empty((n_eval, 8192), dtype=torch.float64, device=dev)
+
+    def put(a, b, T):
+        Te[a:b] = T.double()
+    _glossy_rows(hs, sc, dev, (pos, nrm, view, expo), put)
+    b = bins[s_t, v_t].long()
+    sv = vals[v_t, b].double()                                           # [n, 512] stored bin rows
+    si = idx[v_t, b].long()
+    Tsur = mu[None] + sg * net.forward(raw).double()                     # [n, 512] at isel
+    curves = (512, 1024, 2048, 4096, 8192)
+    sets = [torch.topk(absum, kk).indices for kk in curves]
+    exact = torch.zeros((n_eval, 3), dtype=torch.float64, device=dev)
+    plain, sur, trunc = torch.zeros_like(exact), torch.zeros_like(exact), torch.zeros_like(exact)
+    tk = [torch.zeros_like(exact) for _ in curves]
+    for s in range(S):
+        m = s_t == s
+        if not bool(m.any()):
+            continue
+        L = Lk[s]                                                        # [8192, 3]
+        exact[m] = Te[m] @ L
+        plain[m] = torch.einsum("nj,njc->nc", sv[m], L[si[m]])
+        sur[m] = Tsur[m] @ L[isel]
+        trunc[m] = Te[m][:, isel] @ L[isel]
+        for q, ik in enumerate(sets):
+            tk[q][m] = Te[m][:, ik] @ L[ik]
+    rel = lambda x, y: float((x - y).norm() / y.norm())
+    curve = [{"index_set": kk, "rel_l2_vs_untruncated": rel(t, exact)} for kk, t in zip(curves, tk)]
+    return {"samples": f"{n_eval} random (vertex, pair) of the 100000 x 32 frame",
+            "rel_l2_vs_plain": rel(sur, plain), "rel_l2_vs_untruncated": rel(sur, exact),
+            "plain_vs_untruncated": rel(plain, exact),
+            "index_set_floor_vs_untruncated": rel(trunc, exact),
+            "index_set_curve": curve}
 
 
 def measure_rows(hs, dev, flush, only=None):
@@ -257,6 +615,24 @@ def measure_rows(hs, dev, flush, only=None):
 
     def want(name):
         return only is None or name in only
+
+    # c0: one fractional shift of a one-channel 32x32 map + dense FP32 shading of 1000 sphere
+    # vertices (1024 coefficients each): a launch-bound frame
+    if want("c0"):
+        sc0 = synth.scene(0)
+        L0 = hs.haar_forward(torch.tensor(sc0["light"], dtype=torch.float32, device=dev))
+        w = synth.transport_weights(sc0["pos"], sc0["nrm"], sc0["occ_c"], sc0["occ_r"], 32, 32, device=dev,
+                                    dtype=torch.float32).contiguous()
+        T0 = hs.haar_forward(w)
+        prm0 = torch.tensor(sc0["params"], dtype=torch.float64, device=dev)
+        plan = hs.Plan(32, 32, 1, max_shifts=1)
+        tr = hs.Transport(hs.HAAR_T_DENSE_F32, 1000, 1024, T0)
+        R0 = torch.empty((1000, 1, 1), dtype=torch.float32, device=dev)
+        ms = _timeit(lambda: hs.shade_batch(plan, L0, prm0, tr, R0), 20, flush, stream)
+        rows["c0"] = {"what": "c0 frame: 1 shift of a 1-channel 32x32 map + dense FP32 shading of 1000 vertices "
+                              "(shade_batch: set-up, shift, shade)", "frame_ms": ms,
+                      "value": 1000 / ms / 1e3, "unit": UNIT, "bound": "launch latency (4 KB map, 4 MB transport)"}
+        plan.close()
 
     # S2 / S4 roofline: 4096 translations of the RGB 128x256 map, full FP32 output (1.6 GB)
     if want("translation_shift_batch"):
@@ -559,7 +935,7 @@ def measure_rows(hs, dev, flush, only=None):
 
     # c3 frame: view bins + 32 rotations (FP32 SKC4) + view-binned top-512 FP16 shading
     c3 = None
-    if want("c3_bincsr") or want("c4_surrogate") or want("surrogate_training"):
+    if want("c3_bincsr") or want("c4_surrogate") or want("surrogate_training") or want("glossy_coefficient_sweep"):
         sc3 = synth.scene(3)
         V, S = sc3["V"], sc3["S"]
         vals, idx, absum = _glossy_transport(hs, sc3, dev)
@@ -587,56 +963,146 @@ def measure_rows(hs, dev, flush, only=None):
                                  "frame_ms": ms_frame, "value": plain_c3, "unit": UNIT,
                                  "kernel": "k_shade_bincsr_f16", "kernel_ms": ms_shade,
                                  "achieved_gbs": byt / ms_shade / 1e6, "frac_hbm": byt / ms_shade / 1e6 / hbm,
-                                 "distinct_vertex_bins": distinct}
-        del vals, idx, tr, R
+                                 "distinct_vertex_bins": distinct,
+                                 "transport": "per (vertex, bin) the top 512 of the lowest 8192 coefficients (Phong "
+                                              "transfer integrated on the 64x128 grid: levels 1-2 of the 256x512 map "
+                                              "are zero, so no stored index is finer than level 3)"}
+        del tr, R
         c3 = True
 
+    # N3 with glossiness: the c3 frame's view-binned shading from the top-K of
+    # each stored row, K = 16 .. 512, for Phong exponents 8, 32 and 128 (every
+    # vertex at that exponent); time of the shading kernel and rel-L2 of the
+    # radiance against the untruncated product (all 8192 coefficients of the
+    # same bin's transport) on sampled (vertex, pair)
+    if c3 and want("glossy_coefficient_sweep"):
+        sweep = []
+        rng = np.random.default_rng(47)
+        ns = 4096
+        vs_ = torch.tensor(rng.integers(0, V, ns), device=dev)
+        ss_ = torch.tensor(rng.integers(0, S, ns), device=dev)
+        Lk = lit.reshape(S, -1, 4)[:, :8192, :3].double()
+        Rk = torch.empty((V, S, 3), dtype=torch.float32, device=dev)
+        for ex in (8.0, 32.0, 128.0):
+            gv, gi, _ = _glossy_transport(hs, sc3, dev, K=512, expo=ex, by_magnitude=True)
+            b_ = bins[ss_, vs_].long()
+            vsn, bsn = vs_.cpu().numpy(), b_.cpu().numpy()
+            view = synth.bin_view_world(sc3["nrm"][vsn], 16)[np.arange(ns), bsn]
+            Tf = torch.empty((ns, 8192), dtype=torch.float64, device=dev)
+
+            def putf(a, b, T):
+                Tf[a:b] = T.double()
+            _glossy_rows(hs, sc3, dev, (sc3["pos"][vsn], sc3["nrm"][vsn], view, np.full(ns, ex)), putf)
+            full = torch.zeros((ns, 3), dtype=torch.float64, device=dev)
+            for s_ in range(S):
+                m = ss_ == s_
+                if bool(m.any()):
+                    full[m] = Tf[m] @ Lk[s_]
+            levels = []
+            for K in (16, 32, 64, 128, 256, 512):
+                ik, perm = torch.sort(gi[..., :K], dim=2)
+                vk = torch.gather(gv[..., :K], 2, perm).contiguous()
+                trk = hs.Transport(hs.HAAR_T_BINCSR_F16_U32, V, K, vk, ik.contiguous(), bins=16, bin_of=bins)
+                ms = _timeit(lambda: hs.shade_vertices(plan, trk, lit, S, Rk), 5, flush, stream)
+                got = Rk[vs_, ss_].double()
+                levels.append({"K": K, "shade_ms": ms,
+                               "rel_l2_vs_untruncated": float((got - full).norm() / full.norm())})
+                del trk, vk, ik, perm
+            sweep.append({"phong_exponent": ex, "levels": levels})
+            del gv, gi, Tf
+        rows["glossy_coefficient_sweep"] = {"what": "c3 frame shaded from the top-K of each view-binned row "
+                                                    "(every vertex at one Phong exponent), shading kernel time "
+                                                    "and error against the bin's untruncated transport "
+                                                    f"({ns} sampled (vertex, pair))", "exponents": sweep}
+
     if c3 and (want("c4_surrogate") or want("surrogate_training")):
-        # c4 frame: the same 32 rotations, transport from the surrogate (random-init
-        # weights, index set = 512 largest mean |T| of the c3 transports), fused shading
+        # S8 + c4: train the surrogate on transports of the glossy scene (random
+        # (vertex, camera) pairs, Phong transfer on the 64x128 grid projected by
+        # haar_forward), index set = the 512 largest mean |T|; then the c4 frame:
+        # the same 32 rotations, transport from the trained surrogate fused with
+        # the shading, and its accuracy against the stored-transport frame
+        from paper_1705_07272_gb300 import training
         K = 512
-        isel = torch.sort(torch.topk(absum, K).indices).values.to(torch.int32)
-        mu = torch.zeros(K, dtype=torch.float32, device=dev)
-        sg = torch.full((K,), 1e-3, dtype=torch.float32, device=dev)
+        n_train = int(os.environ.get("HAAR_SURROGATE_SAMPLES", "2000000"))
+        rng = np.random.default_rng(41)
+        raw_tr, gen_tr = _glossy_pairs(rng, sc3, n_train)
+        nt = 8192
+        s1 = torch.zeros(nt, dtype=torch.float64, device=dev)
+        s2 = torch.zeros(nt, dtype=torch.float64, device=dev)
+        sa = torch.zeros(nt, dtype=torch.float64, device=dev)
+
+        def acc_moments(a, b, T):
+            s1.add_(T.sum(0).double())
+            s2.add_((T.double() ** 2).sum(0))
+            sa.add_(T.abs().sum(0).double())
+        t0 = time.perf_counter()
+        _glossy_rows(hs, sc3, dev, gen_tr, acc_moments)
+        isel = torch.sort(torch.topk(sa, K).indices).values
+        mu64 = s1[isel] / n_train
+        sg64 = torch.sqrt(torch.clamp((s2[isel] / n_train - mu64 ** 2).mean(), min=1e-30))
+        Y = torch.empty((n_train, K), dtype=torch.float32, device=dev)
+
+        def targets(a, b, T):
+            Y[a:b] = ((T[:, isel].double() - mu64) / sg64).float()
+        _glossy_rows(hs, sc3, dev, gen_tr, targets)
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        raw_g = torch.tensor(raw_tr, dtype=torch.float32, device=dev)
         net = hs.Surrogate(max_batch=8192, max_rows=262144, max_groups=S)
-        rng = np.random.default_rng(4)
-        flat = []
-        for fi, fo in ((320, 256), (256, 256), (256, 256), (256, 256), (256, 512)):
-            flat += [rng.standard_normal(fo * fi) * math.sqrt(2.0 / fi), np.zeros(fo)]
-        net.set_params(torch.tensor(np.concatenate(flat), dtype=torch.float32, device=dev))
+        net.set_params(torch.tensor(_init_params(np.random.default_rng(4)), dtype=torch.float32, device=dev))
+        epochs = int(os.environ.get("HAAR_SURROGATE_EPOCHS", "30"))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        last_loss = training.fit(net, raw_g, Y, epochs=epochs, batch=8192, lr=(2e-3, 6e-4, 2e-4))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del Y, raw_g
+        mu = mu64.float().contiguous()
+        sg = sg64.float().expand(K).contiguous()
+        isel32 = isel.to(torch.int32)
         R4 = torch.empty((V, S, 3), dtype=torch.float32, device=dev)
         N3 = 131072
         strides = (N3 * 4, 1, 4)                    # SKC4 lighting
+        hs.haar_shift(plan, L3, eul3, lit)
+        acc = _surrogate_accuracy(hs, net, sc3, dev, lit, bins, vals, idx, isel, mu64, sg64, sa)
         if want("c4_surrogate"):
             def c4_frame():
                 hs.haar_shift(plan, L3, eul3, lit)
-                net.shade(pos, nrm, cams, mu, sg, isel, lit, 3, strides, R4)
+                net.shade(pos, nrm, cams, mu, sg, isel32, lit, 3, strides, R4)
             ms_frame = _timeit(c4_frame, 5, flush, stream)
-            ms_mlp = _timeit(lambda: net.shade(pos, nrm, cams, mu, sg, isel, lit, 3, strides, R4), 5, flush, stream)
+            ms_mlp = _timeit(lambda: net.shade(pos, nrm, cams, mu, sg, isel32, lit, 3, strides, R4), 5, flush, stream)
             mlp_flops = 2.0 * V * S * (320 * 256 + 3 * 256 * 256 + 256 * 3)
             rows["c4_surrogate"] = {"what": "c4 frame: 32 rotations + surrogate transport (4x256 GELU MLP, bf16 tcgen05) "
-                                            "fused with shading",
+                                            "fused with shading, trained weights",
                                     "frame_ms": ms_frame, "value": V * S / ms_frame / 1e3, "unit": UNIT,
                                     "kernel": "haar_mlp_shade", "kernel_ms": ms_mlp,
                                     "achieved_tflops": mlp_flops / ms_mlp / 1e9,
                                     "frac_tensor": mlp_flops / ms_mlp / 1e9 / bf16_peak,
                                     "vs_plain_c3_frame": (V * S / ms_frame / 1e3) / plain_c3,
-                                    "weights": "random init (throughput only)"}
+                                    "weights": f"trained: {n_train} transports, {epochs} epochs of batch 8192, "
+                                               f"last-epoch loss {last_loss:.4f}",
+                                    "accuracy": acc,
+                                    "storage_bytes": {"surrogate_weights_bf16": int(net.n_params) * 2,
+                                                      "view_binned_transport": V * 16 * 512 * 6}}
         if want("surrogate_training"):
-            # S8: one Adam training step on a batch of 8192
+            # S8: one Adam training step on a batch of 8192, and the whole training run above
             B = 8192
             raw = torch.randn((B, 9), dtype=torch.float32, device=dev)
             tgt = torch.randn((B, 512), dtype=torch.float32, device=dev)
-            ms_eager = _timeit(lambda: net.train_step(raw, tgt, 1e-4), 10, flush, stream)
-            graph, _ = net.capture_train_step(raw, tgt, 1e-4)
+            ms_eager = _timeit(lambda: net.train_step(raw, tgt, 1e-7), 10, flush, stream)
+            graph, _ = net.capture_train_step(raw, tgt, 1e-7)
             ms_train = _timeit(graph.replay, 10, flush, stream)
             tflops = 3.0 * 2.0 * B * (320 * 256 + 3 * 256 * 256 + 256 * 512) / ms_train / 1e9
             rows["surrogate_training"] = {"what": "haar_mlp_train_step, batch 8192 (forward, backward, Adam), "
-                                                  "replayed from a CUDA graph",
+                                                  "replayed from a CUDA graph; and the c4 training run",
                                           "ms": ms_train, "eager_ms": ms_eager, "samples_per_s": B / ms_train * 1e3,
-                                          "achieved_tflops": tflops, "frac_tensor": tflops / bf16_peak}
+                                          "achieved_tflops": tflops, "frac_tensor": tflops / bf16_peak,
+                                          "training_run": {"samples": n_train, "epochs": epochs,
+                                                           "data_s": t_data, "train_s": t_train,
+                                                           "last_epoch_loss": last_loss}}
         net.close()
     if c3:
+        del vals, idx
         plan.close()
     return rows
 
@@ -718,9 +1184,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    cpu = None
+    cpu, checks = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the host-side leg: the oracle's timed frame sample and the oracle's
+        # results for the rows' accuracy checks, all before any GPU work
         cpu = cpu_baseline(args.cpu_sample)
+        checks = oracle_checks()
 
     import torch
     import paper_1705_07272_gb300 as hs
@@ -831,19 +1300,22 @@ def main():
     rows = None
     if rank == 0 and not args.no_rows:
         rows = measure_rows(hs, dev, flush)
+    acc = gpu_checks(hs, dev, checks) if checks is not None else None
+    if acc is not None and rows is not None:
+        for name, r in acc.items():
+            if name in rows:
+                rows[name]["accuracy"] = r
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "H": wl["H"], "W": wl["W"], "channels": wl["C"],
-                           "shifts_per_step": wl["S"], "vertices_per_gpu": wl["V"], "topk": wl["K"],
-                           "l2": "flushed between timed steps (256 MiB write)",
-                           "parallelism": f"{world} independent vertex shards (no collective)"},
+                "config": bench_config(world),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "d2h": "radiance written by the shading kernel into pinned host memory"},
-                "gpu_launches": 3 * args.steps, "clocks": clk, "rows": rows}
+                "gpu_launches": 3 * args.steps, "clocks": clk,
+                "accuracy": None if acc is None else acc["c1"], "rows": rows}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
