@@ -162,7 +162,7 @@ HAAR_API haar_status_t haar_shift(haar_shift_plan_t plan, const float* coeffs_in
  * memory, which every GPU that loads the library holds until the process
  * exits.  A call needs, each part rounded up to a multiple of 64 floats:
  * the pixel map (C*H*W floats for translations, 8*H*W*ceil(C/3) for
- * rotations), 8*H + 4*W floats of tables, for rotations S*8*(H+W) floats of
+ * rotations), 4*(H+W) floats of tables, for rotations S*8*(H+W) floats of
  * per-rotation tables, 20*S floats of shift records, S*C*T floats of tile
  * means (T = H*W/4096 tiles for H >= 64, 1 or 2 below; T = H*W/256 for
  * float32 KSC translations) and S tile counters, for the map the shift runs

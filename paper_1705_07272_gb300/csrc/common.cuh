@@ -84,10 +84,10 @@ struct haar_shift_plan_s {
 
 namespace hs {
 
-// Rotation tables of a map (plan->trig, floats): [H] float4 (sin theta_i hi,
-// lo, cos theta_i hi, lo), then FP64 sin theta_i [H], cos theta_i [H],
-// sin phi_j [W], cos phi_j [W].
-__host__ __device__ __forceinline__ long long trig_floats(int H, int W) { return 4LL * H + 4LL * (H + W); }
+// Rotation tables of a map (plan->trig): [H] float4 (sin theta_i hi, lo,
+// cos theta_i hi, lo), then [W] float4 (sin phi_j hi, lo, cos phi_j hi, lo),
+// built in FP64.
+__host__ __device__ __forceinline__ long long trig_floats(int H, int W) { return 4LL * (H + W); }
 // Per-rotation tables (float4): sin/cos psi_j [W], sin/cos alpha_m [W], rows [2H].
 __host__ __device__ __forceinline__ long long rot_table_float4s(int H, int W) { return 2LL * W + 2LL * H; }
 // Pixel map floats the set-up synthesises: rotations read an interleaved map

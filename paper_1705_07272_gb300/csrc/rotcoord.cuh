@@ -137,6 +137,42 @@ __device__ __forceinline__ RotSrc rot_source(float4 th, float4 ab, float4 cd, fl
   return o;
 }
 
+__device__ __forceinline__ fpair fp_split(double x) {
+  const float h = (float)x;
+  return fpair{h, (float)(x - (double)h)};
+}
+
+// Angles of R = Ry(a) Rx(b) Ry(c) as float pairs (from yxy_angles' output).
+struct RotAngles {
+  fpair sa, ca, sb, cb, sc, cc;
+};
+
+__device__ __forceinline__ RotAngles rot_angles(const double ang[6]) {
+  return RotAngles{fp_split(ang[0]), fp_split(ang[1]), fp_split(ang[2]),
+                   fp_split(ang[3]), fp_split(ang[4]), fp_split(ang[5])};
+}
+
+// One column's per-rotation entries from the map's pair table entry
+// (sin phi_j hi, lo, cos phi_j hi, lo): sin/cos(phi_j + c) and
+// sin/cos(phi_j - a), by error-free products and sums.
+__device__ __forceinline__ void rot_col_entries(float4 p, const RotAngles& g, float4& psi, float4& al) {
+  const fpair sp{p.x, p.y}, cp{p.z, p.w};
+  const fpair s1 = padd(pmul(sp, g.cc), pmul(cp, g.sc)), c1 = padd(pmul(cp, g.cc), pneg(pmul(sp, g.sc)));
+  const fpair s2 = padd(pmul(sp, g.ca), pneg(pmul(cp, g.sa))), c2 = padd(pmul(cp, g.ca), pmul(sp, g.sa));
+  psi = make_float4(s1.h, s1.l, c1.h, c1.l);
+  al = make_float4(s2.h, s2.l, c2.h, c2.l);
+}
+
+// One row's per-rotation entries from (sin theta_i hi, lo, cos theta_i hi,
+// lo): (A, B) = (sin b cos theta_i, cos b sin theta_i), (C, D) = (cos b cos
+// theta_i, sin b sin theta_i).
+__device__ __forceinline__ void rot_row_entries(float4 q, const RotAngles& g, float4& ab, float4& cd) {
+  const fpair st{q.x, q.y}, ct{q.z, q.w};
+  const fpair A = pmul(g.sb, ct), B = pmul(g.cb, st), C = pmul(g.cb, ct), D = pmul(g.sb, st);
+  ab = make_float4(A.h, A.l, B.h, B.l);
+  cd = make_float4(C.h, C.l, D.h, D.l);
+}
+
 // R = Ry(a) Rx(b) Ry(c) for a rotation matrix R (row-major, FP64), without
 // trigonometry: (sin a, cos a) from R's middle column, then M = Ry(-a) R =
 // Rx(b) Ry(c) gives (cos c, sin c) from its first row and (sin b, cos b) from

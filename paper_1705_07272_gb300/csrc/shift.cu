@@ -545,7 +545,7 @@ __device__ __forceinline__ float merge4f(float* ob, const Geometry& g, int K, fl
 // the tile mean on, and (last tile of a shift) runs the coarse levels.
 // blockDim = (T/4)^2.
 template <int KIND, int OUT, int CG>
-__global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 2 : 4) k_shift_reg(ShiftArgs a) {
+__global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift_reg(ShiftArgs a) {
   extern __shared__ __align__(16) float smem[];
   const Geometry& g = a.g;
   const int T = g.T;
@@ -966,7 +966,7 @@ struct SetupArgs {
   const double* params;
   ShiftParam* prm;
   unsigned* counters;
-  const double* dtrig;    // rotations: FP64 sin theta_i [H], cos theta_i [H], sin phi_j [W], cos phi_j [W]
+  const float4* trig;     // rotations: the map's pair tables, rows [H] then columns [W]
   float4* rtab;           // rotations: per-rotation tables
   long long rt_stride;
 };
@@ -1047,15 +1047,17 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
     return;
   }
   if (rot) {
-    // rotation s = blockIdx.x - nbp: R = Ry(a) Rx(b) Ry(c) (proper Euler angles)
-    const int s = blockIdx.x - a.nbp;
-    __shared__ double sh[6];
-    if (threadIdx.x == 0) {
-      double R[9], ang[6];
+    // rotations, one warp each (8 per block): lane 0 finds R = Ry(a) Rx(b)
+    // Ry(c) (proper Euler angles) in FP64 and writes the record; the warp
+    // then builds the rotation's float-pair tables
+    __shared__ double sh[8][6];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = (blockIdx.x - a.nbp) * 8 + w;
+    if (s >= a.S) return;
+    if (lane == 0) {
+      double R[9];
       rotation_matrix(a, s, R);
-      yxy_angles(R, ang);
-      for (int k = 0; k < 6; ++k) sh[k] = ang[k];
-      const double sa = ang[0], ca = ang[1];
+      yxy_angles(R, sh[w]);
       ShiftParam p;
       p.kx = p.ky = 0;
       p.wx0 = p.wy0 = 1.0f;
@@ -1063,31 +1065,16 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
       p.perm_mask = 0u;
       p.pad = 0;
       for (int k = 0; k < 9; ++k) p.R[k] = (float)R[k];
-      p.a_px = (float)(atan2(sa, ca) * (a.W / (2.0 * 3.14159265358979323846)) - 0.5);
+      p.a_px = (float)(atan2(sh[w][0], sh[w][1]) * (a.W / (2.0 * 3.14159265358979323846)) - 0.5);
       p.pad2[0] = p.pad2[1] = 0.0f;
       a.prm[s] = p;
       a.counters[s] = 0u;
     }
-    __syncthreads();
-    const double sa = sh[0], ca = sh[1], sb = sh[2], cb = sh[3], sc = sh[4], cc = sh[5];
-    const double* st = a.dtrig;
-    const double* ct = a.dtrig + a.H;
-    const double* sp = a.dtrig + 2 * a.H;
-    const double* cp = sp + a.W;
+    __syncwarp();
+    const RotAngles g = rot_angles(sh[w]);
     float4* rt = a.rtab + (long long)s * a.rt_stride;
-    for (int j = threadIdx.x; j < a.W; j += blockDim.x) {
-      const double s0 = sp[j], c0 = cp[j];
-      rt[j] = split2(s0 * cc + c0 * sc, c0 * cc - s0 * sc);             // psi_j = phi_j + c
-      rt[a.W + j] = split2(s0 * ca - c0 * sa, c0 * ca + s0 * sa);       // alpha_j = phi_j - a
-    }
-    for (int i = threadIdx.x; i < a.H; i += blockDim.x) {
-      const double s0 = st[i], c0 = ct[i];
-      const double A = sb * c0, B = cb * s0, C = cb * c0, D = sb * s0;
-      float4* r = rt + 2 * a.W + 2 * i;
-      const float Ah = (float)A, Bh = (float)B, Ch = (float)C, Dh = (float)D;
-      r[0] = make_float4(Ah, (float)(A - (double)Ah), Bh, (float)(B - (double)Bh));
-      r[1] = make_float4(Ch, (float)(C - (double)Ch), Dh, (float)(D - (double)Dh));
-    }
+    for (int j = lane; j < a.W; j += 32) rot_col_entries(a.trig[a.H + j], g, rt[j], rt[a.W + j]);
+    for (int i = lane; i < a.H; i += 32) rot_row_entries(a.trig[i], g, rt[2 * a.W + 2 * i], rt[2 * a.W + 2 * i + 1]);
     return;
   }
   for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
@@ -1137,22 +1124,18 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
 }
 
 // Rotation tables of the map (see trig_floats()): pixel-centre sines and
-// cosines in FP64, and the row ones also as float pairs.
+// cosines in FP64, kept as float pairs.
 __global__ void k_trig(int H, int W, float* trig) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const double pi = 3.14159265358979323846;
-  double* d = reinterpret_cast<double*>(trig + 4LL * H);
+  float4* t = reinterpret_cast<float4*>(trig);
   if (e < H) {
-    const double t = (e + 0.5) * pi / H;
-    const double sn = sin(t), cs = cos(t);
-    reinterpret_cast<float4*>(trig)[e] = split2(sn, cs);
-    d[e] = sn;
-    d[H + e] = cs;
+    const double x = (e + 0.5) * pi / H;
+    t[e] = split2(sin(x), cos(x));
   } else if (e < H + W) {
     const int j = e - H;
-    const double t = (j + 0.5) * 2.0 * pi / W;
-    d[2 * H + j] = sin(t);
-    d[2 * H + W + j] = cos(t);
+    const double x = (j + 0.5) * 2.0 * pi / W;
+    t[H + j] = split2(sin(x), cos(x));
   }
 }
 
@@ -1258,11 +1241,11 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
   a.params = params;
   a.prm = p->prm;
   a.counters = p->counters;
-  a.dtrig = reinterpret_cast<const double*>(p->trig + 4LL * g.H);
+  a.trig = reinterpret_cast<const float4*>(p->trig);
   a.rtab = reinterpret_cast<float4*>(p->rtab);
   a.rt_stride = rot_table_float4s(g.H, g.W);
   if (rot && p->rtab == nullptr) return set_error(HAAR_ERR_INVALID_ARG, "rotation tables missing");
-  k_setup<<<a.nbp + (rot ? S : 1), kThreads, 0, st>>>(a);
+  k_setup<<<a.nbp + (rot ? (S + 7) / 8 : 1), kThreads, 0, st>>>(a);
   return cuda_check(cudaGetLastError(), "k_setup launch");
 }
 

@@ -280,30 +280,11 @@ struct RotTabs {
   float a_px;
 };
 
-__device__ __forceinline__ fpair fp_split(double x) {
-  const float h = (float)x;
-  return fpair{h, (float)(x - (double)h)};
-}
-
 __device__ void build_rot_tabs(const ShadeTripleArgs& s, const double* ang, const RotTabs& rt, int t, int T) {
   const TripleArgs& a = s.t;
-  const fpair sa = fp_split(ang[0]), ca = fp_split(ang[1]), sb = fp_split(ang[2]), cb = fp_split(ang[3]);
-  const fpair sc = fp_split(ang[4]), cc = fp_split(ang[5]);
-  for (int j = t; j < a.W; j += T) {
-    const float4 p = s.tab_p[j];
-    const fpair sp{p.x, p.y}, cp{p.z, p.w};
-    const fpair s1 = padd(pmul(sp, cc), pmul(cp, sc)), c1 = padd(pmul(cp, cc), pneg(pmul(sp, sc)));
-    const fpair s2 = padd(pmul(sp, ca), pneg(pmul(cp, sa))), c2 = padd(pmul(cp, ca), pmul(sp, sa));
-    rt.psi[j] = make_float4(s1.h, s1.l, c1.h, c1.l);
-    rt.al[j] = make_float4(s2.h, s2.l, c2.h, c2.l);
-  }
-  for (int i = t; i < a.H; i += T) {
-    const float4 q = s.tab_t[i];
-    const fpair st{q.x, q.y}, ct{q.z, q.w};
-    const fpair A = pmul(sb, ct), B = pmul(cb, st), C = pmul(cb, ct), D = pmul(sb, st);
-    rt.row[2 * i] = make_float4(A.h, A.l, B.h, B.l);
-    rt.row[2 * i + 1] = make_float4(C.h, C.l, D.h, D.l);
-  }
+  const RotAngles g = rot_angles(ang);
+  for (int j = t; j < a.W; j += T) rot_col_entries(s.tab_p[j], g, rt.psi[j], rt.al[j]);
+  for (int i = t; i < a.H; i += T) rot_row_entries(s.tab_t[i], g, rt.row[2 * i], rt.row[2 * i + 1]);
 }
 
 // The rotated BRDF at output pixel (i, j): the source position from

@@ -197,18 +197,25 @@ def _glossy_dataset(n, seed, device="cuda", chunk=8192):
                                     view=view[a:a + chunk], expo=expo[a:a + chunk], device=device)
         Ts.append(oh.forward(w.double().cpu().numpy()) / 4.0)
     raw = np.concatenate([pos, nrm, view], axis=1).astype(np.float32)
-    return raw, np.concatenate(Ts), sc
+    return raw, np.concatenate(Ts), sc, (vid, cams)
 
 
 def test_trained_surrogate_against_stored_transport(hs):
-    # Train the surrogate on oracle transports (S8), then compare its shading
-    # with the stored-transport method on held-out (vertex, view) pairs under
-    # rotated lighting.  What the network gains: 1.6 MB of weights instead of
-    # 4.9 GB of view-binned transport for the 100k-vertex scene, and
-    # continuous views instead of 16 bins; the accuracy cost is reported.
+    # Train the surrogate on oracle transports (S8), then compare, on held-out
+    # (vertex, camera) pairs under rotated lighting, three ways of shading
+    # against the transport at the exact view, untruncated:
+    #   the surrogate (512 coefficients at a fixed index set),
+    #   the plain stored method (16 view bins x top-512 FP16 per vertex),
+    #   the mean transport (no network).
+    # The view binning costs the stored method far more than the network
+    # costs the surrogate (glossy lobes up to s = 128 move between bins), so
+    # the surrogate must beat it clearly; its own error stays above the
+    # 512-index set's truncation floor.
     import torch
+    from oracle import transport as otr2
+    from paper_1705_07272_gb300 import training
     n_train, n_test = 131072, 4096
-    raw, T, sc = _glossy_dataset(n_train + n_test, 7)
+    raw, T, sc, (vid, cams) = _glossy_dataset(n_train + n_test, 7)
     Ttr = T[:n_train]
     idx = np.sort(np.argsort(-np.abs(Ttr).mean(axis=0), kind="stable")[:512])
     mu = Ttr[:, idx].mean(axis=0)
@@ -216,34 +223,44 @@ def test_trained_surrogate_against_stored_transport(hs):
     # share of the transport's energy, as the shading error does
     sg = np.full(512, Ttr[:, idx].std() + 1e-12)
     Y = ((T[:, idx] - mu) / sg).astype(np.float32)
-    rng = np.random.default_rng(11)
-    P = om.init(rng)
     net = hs.Surrogate(max_batch=4096, max_rows=4096, max_groups=8)
-    net.set_params(_t(_flat(P), None).float())
-    Rg, Yg = _t(raw[:n_train]), _t(Y[:n_train])
-    B = 4096
-    steps = 4000
-    for it in range(steps):
-        lr = 1e-3 if it < steps // 2 else (3e-4 if it < 3 * steps // 4 else 1e-4)
-        sel = torch.randint(0, n_train, (B,), device="cuda")
-        net.train_step(Rg[sel].contiguous(), Yg[sel].contiguous(), lr)
+    net.set_params(_t(_flat(om.init(np.random.default_rng(11))), None).float())
+    training.fit(net, _t(raw[:n_train]), _t(Y[:n_train]), epochs=120, batch=4096, lr=(2e-3, 6e-4, 2e-4))
     out = net.forward(_t(raw[n_train:])).cpu().numpy().astype(np.float64)
     assert net.status() == 0
+    # the plain method's stored row for each test pair: the bin the camera
+    # falls in, its transport at the bin's direction, top-512 in FP16
+    te = slice(n_train, None)
+    pos, nrm = sc["pos"][vid[te]], sc["nrm"][vid[te]]
+    dirs = synth.view_bin_dirs(16)
+    bins = np.array([otr2.view_bins(pos[k:k + 1], nrm[k:k + 1], cams[te][k:k + 1], dirs)[0][0, 0]
+                     for k in range(n_test)])
+    bview = synth.bin_view_world(nrm, 16)[np.arange(n_test), bins]
+    w = synth.transport_weights(pos, nrm, sc["occ_c"], sc["occ_r"], 64, 128, view=bview,
+                                expo=sc["expo"][vid[te]], device="cuda")
+    Tb = oh.forward(w.double().cpu().numpy()) / 4.0
+    bv, bi, bp = otr2.topk_csr(Tb, 512)
+    Tbin = otr2.csr_dense(otr2.to_f16(bv), bi, bp, 8192)
     # shading under 3 rotations of the c4 lighting
     H, W = 256, 512
     L = oh.forward(sc["light"])
     eul = synth.euler_angles(np.random.default_rng(3), 3)
     Ls = osh.haar_shift(L, H, W, osh.ROTATE_EULER, eul)[..., :8192]         # [3, C, 8192]
     Tte = T[n_train:]
-    plain = np.einsum("nk,sck->nsc", Tte, Ls)
-    trunc = np.einsum("nk,sck->nsc", Tte[:, idx], Ls[..., idx])
+    exact = np.einsum("nk,sck->nsc", Tte, Ls)
+    plain = np.einsum("nk,sck->nsc", Tbin, Ls)
+    floor = np.einsum("nk,sck->nsc", Tte[:, idx], Ls[..., idx])
     mean_only = np.einsum("k,sck->sc", mu, Ls[..., idx])[None].repeat(n_test, 0)
     sur = np.einsum("nk,sck->nsc", mu + sg * out, Ls[..., idx])
-    e_sur, e_trunc, e_mean = rel_l2(sur, plain), rel_l2(trunc, plain), rel_l2(mean_only, plain)
-    print(f"surrogate vs stored transport: rel-L2 {e_sur:.3e} (index-set truncation alone {e_trunc:.3e}, "
-          f"mean transport {e_mean:.3e})")
+    e_sur, e_plain = rel_l2(sur, exact), rel_l2(plain, exact)
+    e_floor, e_mean = rel_l2(floor, exact), rel_l2(mean_only, exact)
+    print(f"against the exact-view transport: surrogate {e_sur:.3e}, 16-bin stored transport {e_plain:.3e}, "
+          f"512-index floor {e_floor:.3e}, mean transport {e_mean:.3e}")
     stored = 100000 * 16 * 512 * 6
     weights = int(hs.lib().haar_mlp_param_count()) * 2
     assert stored / weights > 1000
+    # measured: surrogate 0.21, stored 0.50, floor 0.051, mean 0.80
+    assert e_floor <= e_sur <= 0.25
+    assert e_sur < 0.6 * e_plain
     assert e_sur < 0.5 * e_mean
     net.close()
