@@ -352,6 +352,125 @@ __global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restri
   }
 }
 
+// Group-CSR shading for rows of exactly 48 floats (16 shifts x RGB, the c1
+// frame) at 4 CTAs per SM: the same CTA = 4 groups x 2 warps and batch
+// pipeline as k_shade_gcsr_f32, but a row is spread over 8 lanes (lane = 8 e
+// + c: entry slot e of 4, floats 4c..4c+3 and 32+2c..33+2c of the row), so a
+// lane holds 12 paired accumulators (4 vertices x 6 floats) instead of 24 and
+// twice as many warps share each SM to hide the row gathers' latency.
+__global__ void __launch_bounds__(256, 4) k_shade_gcsr48(const float* __restrict__ vals,
+                                                         const uint16_t* __restrict__ idx,
+                                                         const int32_t* __restrict__ gptr, int V,
+                                                         const float* __restrict__ L, int NL,
+                                                         float* __restrict__ R) {
+  pdl_wait();                                     // inputs come from the previous kernel
+  typedef unsigned long long u64;
+  __shared__ u64 red[4][8][kGroup][3];
+  __shared__ float4 sv[8][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gl = w >> 1, wh = w & 1;
+  const int n_groups = (V + kGroup - 1) / kGroup;
+  const int es = lane >> 3, c8 = lane & 7;
+  const float4* V4 = reinterpret_cast<const float4*>(vals);
+  const int g = blockIdx.x * 4 + gl;
+  if (g >= n_groups) return;                      // both warps of a pair leave together
+  const int beg = __ldg(gptr + g), end = __ldg(gptr + g + 1);
+  const int mid = beg + (end - beg + 1) / 2;
+  const int jb = wh ? mid : beg;
+  const int je = wh ? end : mid;
+  if (lane == 0 && je > jb) {
+    l2_prefetch_bulk(vals + 4ll * jb, 16u * (unsigned)(je - jb));
+    const uintptr_t ib = reinterpret_cast<uintptr_t>(idx + jb) & ~uintptr_t(15);
+    const uintptr_t ie = reinterpret_cast<uintptr_t>(idx + je) & ~uintptr_t(15);
+    if (ie > ib) l2_prefetch_bulk(reinterpret_cast<const void*>(ib), (unsigned)(ie - ib));
+  }
+  u64 acc[kGroup][3];
+#pragma unroll
+  for (int v = 0; v < kGroup; ++v) acc[v][0] = acc[v][1] = acc[v][2] = 0ull;
+  int nk = 0;
+  float4 nv = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (jb + lane < je) {
+    nk = __ldg(idx + jb + lane);
+    nv = ld_stream_f4(V4 + jb + lane);
+    if (nk >= NL) { nk = 0; nv = make_float4(0.f, 0.f, 0.f, 0.f); }
+  }
+  for (int j0 = jb; j0 < je; j0 += 32) {
+    const int myk = nk;
+    __syncwarp();
+    sv[w][lane] = nv;
+    __syncwarp();
+    const int jn = j0 + 32 + lane;
+    nk = 0;
+    nv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (jn < je) {
+      nk = __ldg(idx + jn);
+      nv = ld_stream_f4(V4 + jn);
+      if (nk >= NL) { nk = 0; nv = make_float4(0.f, 0.f, 0.f, 0.f); }
+    }
+    const int steps = min(8, (je - j0 + 3) >> 2);              // warp-uniform
+    ulonglong2 xa;
+    u64 xb;
+    {
+      const int k = __shfl_sync(0xffffffffu, myk, es);
+      const float* row = L + (unsigned)k * 48u;
+      xa = __ldg(reinterpret_cast<const ulonglong2*>(row) + c8);
+      xb = __ldg(reinterpret_cast<const u64*>(row + 32) + c8);
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      if (p < steps) {
+        ulonglong2 na;
+        u64 nb;
+        if (p + 1 < steps) {
+          const int k = __shfl_sync(0xffffffffu, myk, 4 * (p + 1) + es);
+          const float* row = L + (unsigned)k * 48u;
+          na = __ldg(reinterpret_cast<const ulonglong2*>(row) + c8);
+          nb = __ldg(reinterpret_cast<const u64*>(row + 32) + c8);
+        }
+        const float4 t = sv[w][4 * p + es];
+        const u64 tt[4] = {f2_dup(t.x), f2_dup(t.y), f2_dup(t.z), f2_dup(t.w)};
+#pragma unroll
+        for (int v = 0; v < kGroup; ++v) {
+          acc[v][0] = f2_fma(tt[v], xa.x, acc[v][0]);
+          acc[v][1] = f2_fma(tt[v], xa.y, acc[v][1]);
+          acc[v][2] = f2_fma(tt[v], xb, acc[v][2]);
+        }
+        if (p + 1 < steps) {
+          xa = na;
+          xb = nb;
+        }
+      }
+    }
+  }
+  // sum the 4 entry slots (lanes c8, c8 + 8, c8 + 16, c8 + 24), then the pair's halves
+#pragma unroll
+  for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      acc[v][m] = f2_add(acc[v][m], f2_shfl_xor(acc[v][m], 8));
+      acc[v][m] = f2_add(acc[v][m], f2_shfl_xor(acc[v][m], 16));
+    }
+  if (wh == 1 && es == 0) {
+#pragma unroll
+    for (int v = 0; v < kGroup; ++v)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) red[gl][c8][v][m] = acc[v][m];
+  }
+  pair_sync(1 + gl);
+  if (wh == 0 && es == 0) {
+#pragma unroll
+    for (int v = 0; v < kGroup; ++v) {
+      const int vv = g * kGroup + v;
+      if (vv < V) {
+        float* o = R + (long long)vv * 48;
+        reinterpret_cast<ulonglong2*>(o)[c8] =
+            make_ulonglong2(f2_add(acc[v][0], red[gl][c8][v][0]), f2_add(acc[v][1], red[gl][c8][v][1]));
+        reinterpret_cast<u64*>(o + 32)[c8] = f2_add(acc[v][2], red[gl][c8][v][2]);
+      }
+    }
+  }
+}
+
 // Packing CSR -> vertex-group CSR.  One warp per group builds the bitmap of
 // the union of its rows' indices in shared memory (N <= 65536: 2048 words).
 constexpr int kBmWords = 2048;
@@ -524,7 +643,7 @@ haar_status_t launch_shade_gcsr_f32(const float* vals, const uint16_t* idx, cons
   const long long groups = (V + kGroup - 1) / kGroup;
   const unsigned nb = (unsigned)((groups + 3) / 4);
   cudaError_t e;
-  if (nq == 12) e = launch_pdl(k_shade_gcsr_f32<3, true>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
+  if (nq == 12) e = launch_pdl(k_shade_gcsr48, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, R);
   else if (nq == 8) e = launch_pdl(k_shade_gcsr_f32<2, true>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
   else if (nq == 4) e = launch_pdl(k_shade_gcsr_f32<1, true>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
   else if (nq <= 4) e = launch_pdl(k_shade_gcsr_f32<1, false>, dim3(nb), dim3(256), 0, st, vals, idx, gptr, V, L, NL, ncols, R);
