@@ -69,7 +69,9 @@ typedef enum {
 
 typedef enum {
   HAAR_SHIFT_TRANSLATE = 0,   /* params [S][2] float64: (dx, dy) in pixels */
-  HAAR_SHIFT_ROTATE = 1,      /* params [S][9] float64: R row-major, p' = R p */
+  HAAR_SHIFT_ROTATE = 1,      /* params [S][9] float64: R row-major, p' = R p; R must be a
+                                 rotation (orthonormal, det +1) or a positive multiple of one:
+                                 the kernels use its factorisation Ry(a) Rx(b) Ry(c) */
   HAAR_SHIFT_ROTATE_EULER = 2, /* params [S][3] float64: (alpha, beta, gamma),
                                  R = Rz(gamma) Ry(beta) Rx(alpha) (Eq. tRot) */
   HAAR_SHIFT_ROTATE_CHAIN = 3  /* params as ROTATE_EULER; the paper's own route, an

@@ -557,7 +557,8 @@ constexpr uint32_t F_W_BYTES = 256 * 128;    // one weight k-block [256 x 64] bf
 
 struct __align__(8) FBars {
   uint64_t wfull[F_STAGES], wempty[F_STAGES];
-  uint64_t tfull, aready, drain;
+  uint64_t tfull, drain;
+  uint64_t kready[5];              // k-block j of the next MMA's A operand is written (by all epilogue warps)
   uint64_t red[4];                 // per lane quarter: the 4 column groups' partial radiance are in
   uint32_t tmem_base;
   int abort_flag;
@@ -613,7 +614,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       mbar_init(smem_u32(&bars.wempty[i]), 1);
     }
     mbar_init(smem_u32(&bars.tfull), 1);
-    mbar_init(smem_u32(&bars.aready), F_EPI);
+    for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars.kready[i]), F_EPI);
     for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars.red[i]), 3);
     mbar_init(smem_u32(&bars.drain), 1);
     bars.abort_flag = 0;
@@ -621,7 +622,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&bars.tmem_base)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&bars.tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   for (int i = threadIdx.x; i < 4 * WIDTH; i += blockDim.x) {
@@ -669,20 +670,25 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       const uint32_t idesc = make_idesc(BM, 256);
       int stage = 0;
       uint32_t phase = 0;
-      long long step = 0;
+      uint32_t kpar = 0u;                                // bit j: parity of the next completion of kready[j]
       bool ok = true;
       for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        for (int l = 0; l < 4 && ok; ++l, ++step) {
-          if (!mbar_wait(smem_u32(&bars.aready), (uint32_t)(step & 1), status, abort_flag)) { ok = false; break; }
-          fence_after();
+        for (int l = 0; l < 4 && ok; ++l) {
+          // layers alternate between two accumulators, so that a layer's MMAs
+          // run while the epilogue still reads the previous layer's; each
+          // k-block starts as soon as the epilogue warps have written it
+          const uint32_t acc = tmem + (uint32_t)((l & 1) * 256);
           const int nk = (l == 0) ? 5 : 4;
           for (int kb = 0; kb < nk; ++kb) {
+            if (!mbar_wait(smem_u32(&bars.kready[kb]), (kpar >> kb) & 1u, status, abort_flag)) { ok = false; break; }
+            kpar ^= 1u << kb;
+            fence_after();
             if (!mbar_wait(smem_u32(&bars.wfull[stage]), phase, status, abort_flag)) { ok = false; break; }
             fence_after();
             const uint32_t wa = ring + stage * F_W_BYTES;
 #pragma unroll
             for (int k = 0; k < BK / UMMA_K; ++k)
-              mma_bf16(tmem, make_desc(act_s + kb * 16384 + k * UMMA_K * 2), make_desc(wa + k * UMMA_K * 2), idesc,
+              mma_bf16(acc, make_desc(act_s + kb * 16384 + k * UMMA_K * 2), make_desc(wa + k * UMMA_K * 2), idesc,
                        (kb | k) != 0 ? 1u : 0u);
             mma_commit(smem_u32(&bars.wempty[stage]));
             if (++stage == F_STAGES) { stage = 0; phase ^= 1u; }
@@ -711,8 +717,10 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       {
         __syncwarp();
         for (int i = lane; i < 2 * F_COLS; i += 32) {
+          // local column j = 16 kb + m is layer column 64 kb + 16 cg + m
           const int k = i / F_COLS, j = i - k * F_COLS;
-          const float* W = f.weff + ((long long)(k ? s_hi : s_lo) * WIDTH + cg * F_COLS + j) * f.C;
+          const int col = 64 * (j >> 4) + 16 * cg + (j & 15);
+          const float* W = f.weff + ((long long)(k ? s_hi : s_lo) * WIDTH + col) * f.C;
           float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
           w4.x = W[0];
           if (f.C > 1) w4.y = W[1];
@@ -775,7 +783,8 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       fence_before();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars.aready));
+      if (lane == 0)
+        for (int j = 0; j < 5; ++j) mbar_arrive(smem_u32(&bars.kready[j]));
       // ---- layers
       const int r = q * 32 + lane;
       const long long row = row0 + r;
@@ -787,31 +796,36 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
         float acc_c[4] = {0.f, 0.f, 0.f, 0.f};
         int s = 0;
         if (l == 3 && row_ok) s = (int)(row / f.V);
-        const float(*Wt)[4] = sweff[wid][(l == 3 && s != s_lo) ? 1 : 0];   // column c0 + i at [c0 + i - cg F_COLS]
-        for (int cc = 0; cc < F_COLS / 32; ++cc) {
-          const int c0 = cg * F_COLS + cc * 32;
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        const float(*Wt)[4] = sweff[wid][(l == 3 && s != s_lo) ? 1 : 0];   // column 64 kb + 16 cg + m at [16 kb + m]
+        const uint32_t acc_t = tmem + (uint32_t)((l & 1) * 256) + ((uint32_t)(q * 32) << 16);
+        // the warp's 16 columns of each k-block in turn: the next layer's MMA
+        // on k-block kb can start once all epilogue warps have written it
+        for (int kb = 0; kb < 4; ++kb) {
+          const int c0 = 64 * kb + 16 * cg;
+          float v[16];
+          tmem_ld16(acc_t + (uint32_t)c0, v);
           if (l < 3) {
-            uint32_t pk[16];
+            uint32_t pk[8];
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
+            for (int i = 0; i < 16; i += 2) {
               const float2 b2 = *reinterpret_cast<const float2*>(bias + c0 + i);
               const float2 h = u2f(gelu2(f2_add(f2_pack(v[i], v[i + 1]), f2_pack(b2.x, b2.y))));
               __nv_bfloat162 hb = __floats2bfloat162_rn(h.x, h.y);
               pk[i >> 1] = *reinterpret_cast<uint32_t*>(&hb);
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              *reinterpret_cast<uint4*>(act + act_off(r, c0 + 8 * j)) =
-                  make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+            *reinterpret_cast<uint4*>(act + act_off(r, c0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(act + act_off(r, c0 + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            fence_before();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars.kready[kb]));
           } else {
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
+            for (int i = 0; i < 16; i += 2) {
               const float2 b2 = *reinterpret_cast<const float2*>(bias + c0 + i);
               const float2 h = u2f(gelu2(f2_add(f2_pack(v[i], v[i + 1]), f2_pack(b2.x, b2.y))));
-              const float4 wa = *reinterpret_cast<const float4*>(Wt[c0 - cg * F_COLS + i]);
-              const float4 wb = *reinterpret_cast<const float4*>(Wt[c0 - cg * F_COLS + i + 1]);
+              const float4 wa = *reinterpret_cast<const float4*>(Wt[16 * kb + i]);
+              const float4 wb = *reinterpret_cast<const float4*>(Wt[16 * kb + i + 1]);
               acc_c[0] = fmaf(h.y, wb.x, fmaf(h.x, wa.x, acc_c[0]));
               acc_c[1] = fmaf(h.y, wb.y, fmaf(h.x, wa.y, acc_c[1]));
               acc_c[2] = fmaf(h.y, wb.z, fmaf(h.x, wa.z, acc_c[2]));
@@ -819,12 +833,8 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
             }
           }
         }
-        fence_before();
-        if (l < 3) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&bars.aready));
-        } else {
+        if (l == 3) {
+          fence_before();
           // the 4 column groups of this lane quarter meet in group 0, which adds
           // them in a fixed order (deterministic) and writes the radiance
           if (cg > 0) {
@@ -851,7 +861,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
   __syncthreads();
   fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
   }
 }
 
