@@ -210,7 +210,7 @@ haar_status_t launch_shade_triple(int H, int W, int C, int V, const float* light
                                   cudaStream_t st);
 bool ksc_eligible(const haar_shift_desc_t& d, const Geometry& g, int S);
 size_t ksc_means_floats(const Geometry& g, int S);
-size_t ksc_smem_floats(long long n16);
+size_t ksc_smem_floats(long long n16, int planes);
 haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* coeffs,
                              float scale, cudaStream_t st);
 haar_status_t launch_inverse(int H, int W, int batch, const float* coeffs, float* maps,

@@ -41,6 +41,7 @@ struct ShiftArgs {
   const float4* rows;     // rotations: [H] (sin theta_i hi, lo, cos theta_i hi, lo)
   const float4* rtab;     // rotations: per-rotation tables, rt_stride float4 apart
   long long rt_stride;
+  int tab_off;            // rotations, tables in shared memory: their offset in floats
   float scale;
   float u_scale, v_scale; // H/pi, W/(2 pi)
 };
@@ -59,6 +60,14 @@ __device__ __forceinline__ void rot_taps(const RotSrc& o, int H, int W, int boun
   }
   t0 = r0 * W + ((o.c + h0) & (W - 1));
   t1 = r1 * W + ((o.c + h1) & (W - 1));
+}
+
+// One 32-byte texel of the interleaved rotation map in one load (32-byte
+// aligned): v[2c], v[2c+1] = channel c at columns j and j+1.
+__device__ __forceinline__ void ld_texel(const float4* p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
 }
 
 // Bilinear value of channel ci (0..2) of a texel pair (rows t0, t1).
@@ -544,7 +553,10 @@ __device__ __forceinline__ float merge4f(float* ob, const Geometry& g, int K, fl
 // leave, and warp 0 finishes the tile's levels 5-6 from shared memory, hands
 // the tile mean on, and (last tile of a shift) runs the coarse levels.
 // blockDim = (T/4)^2.
-template <int KIND, int OUT, int CG>
+// SMT (rotations): the rotation's anchor-column table and the map's row table
+// are first copied to shared memory, so that the two dependent table lookups
+// of every pixel are shared-memory loads.
+template <int KIND, int OUT, int CG, bool SMT = false>
 __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift_reg(ShiftArgs a) {
   extern __shared__ __align__(16) float smem[];
   const Geometry& g = a.g;
@@ -619,31 +631,44 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift
     const ShiftParam pr = *p;
     const float4* rt = a.rtab + (long long)s * a.rt_stride;
     const float4* tex = reinterpret_cast<const float4*>(a.pix) + (long long)cgrp * g.N * 2;
+    const float4* colal = rt + g.W;
+    const float4* rowtab = a.rows;
+    if constexpr (SMT) {
+      float4* st = reinterpret_cast<float4*>(smem + a.tab_off);
+      for (int e = threadIdx.x; e < g.W + g.H; e += blockDim.x)
+        st[e] = (e < g.W) ? __ldg(rt + g.W + e) : __ldg(a.rows + (e - g.W));
+      __syncthreads();
+      colal = st;
+      rowtab = st + g.W;
+    }
     float4 ps[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) ps[q] = __ldg(rt + j0 + q);
+    // the row loops stay rolled: a row's body (4 pixels' coordinates) is
+    // large, and unrolled copies of it measured slower (instruction fetch stalls)
     float A1[CG][4];
-#pragma unroll
+#pragma unroll 1
     for (int rp = 0; rp < 2; ++rp) {
       float x[CG][8];
-#pragma unroll
+#pragma unroll 1
       for (int rr = 0; rr < 2; ++rr) {
         const int i = i0 + 2 * rp + rr;
         const float4 th = __ldg(a.rows + i), ab = __ldg(rt + 2 * g.W + 2 * i), cd = __ldg(rt + 2 * g.W + 2 * i + 1);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const RotSrc o = rot_source(th, ab, cd, ps[q], rt + g.W, a.rows, pr.a_px, a.u_scale, a.v_scale, g.H, g.W);
+          const RotSrc o = rot_source<!SMT>(th, ab, cd, ps[q], colal, rowtab, pr.a_px, a.u_scale, a.v_scale, g.H, g.W);
           int t0, t1;
           rot_taps(o, g.H, g.W, g.boundary, t0, t1);
-          const float4 p0 = __ldg(tex + 2 * t0), p1 = __ldg(tex + 2 * t1);
+          float e0[8], e1[8];
+          ld_texel(tex + 2 * t0, e0);
+          ld_texel(tex + 2 * t1, e1);
           const float w = hsc;
-          if (0 < cgn) x[0][4 * rr + q] = w * rot_lerp(p0.x, p0.y, p1.x, p1.y, o.fu, o.fv);
-          if (CG > 1 && 1 < cgn) x[CG > 1 ? 1 : 0][4 * rr + q] = w * rot_lerp(p0.z, p0.w, p1.z, p1.w, o.fu, o.fv);
-          if (CG > 2 && 2 < cgn) {
-            const float2 q0 = __ldg(reinterpret_cast<const float2*>(tex + 2 * t0 + 1));
-            const float2 q1 = __ldg(reinterpret_cast<const float2*>(tex + 2 * t1 + 1));
-            x[CG > 2 ? 2 : 0][4 * rr + q] = w * rot_lerp(q0.x, q0.y, q1.x, q1.y, o.fu, o.fv);
-          }
+#pragma unroll
+          for (int ci = 0; ci < CG; ++ci)
+            if (ci < cgn) {
+              const float val = w * rot_lerp(e0[2 * ci], e0[2 * ci + 1], e1[2 * ci], e1[2 * ci + 1], o.fu, o.fv);
+              if (rr == 0) x[ci][q] = val; else x[ci][4 + q] = val;
+            }
         }
       }
       // level 1 of the row pair's two 2 x 2 blocks (pixels pre-scaled by 1/2 on the fast path)
@@ -656,7 +681,8 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift
             const float ea = x[ci][2 * sc], eb = x[ci][2 * sc + 1];
             const float ec = x[ci][4 + 2 * sc], ed = x[ci][4 + 2 * sc + 1];
             const float h = fast ? 1.0f : 0.5f;
-            A1[ci][2 * rp + sc] = h * ((ea + eb) + (ec + ed));
+            const float av = h * ((ea + eb) + (ec + ed));
+            if (rp == 0) A1[ci][sc] = av; else A1[ci][2 + sc] = av;
             D[0][sc] = h * ((eb + ed) - (ea + ec));
             D[1][sc] = h * ((ec + ed) - (ea + eb));
             D[2][sc] = h * ((ea + ed) - (eb + ec));
@@ -779,7 +805,6 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift
 // the workspace; the last tile of a plane group runs the coarse levels of
 // all its planes at once (16 threads per plane).
 constexpr int kKscPlanes = 48;
-constexpr int kKscPitch = kKscPlanes + 1;       // staging row pitch (bank spread)
 
 // shared floats per plane in the coarse pass: the tile-mean image and the
 // scratch image of the next two levels, each rounded to whole float4
@@ -798,14 +823,16 @@ __device__ __forceinline__ int ksc_global_k(const Geometry& g, int kl, int tr, i
   return gl * (1 + b) + (tr * side + r) * (g.W >> lvl) + tc * side + col;
 }
 
-__global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int P) {
+template <int NP>
+__global__ void __launch_bounds__(16 * NP) k_shift_ksc(ShiftArgs a, int P) {
+  constexpr int kPitch = NP + 1;                // staging row pitch (bank spread)
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_last;
   const Geometry& g = a.g;                      // T = 16, Lt = 4
   const int tile = blockIdx.x;
   const int tr = tile / g.tiles_c, tc = tile - tr * g.tiles_c;
-  const int p0 = blockIdx.y * kKscPlanes;
-  const int PG = min(kKscPlanes, P - p0);
+  const int p0 = blockIdx.y * NP;
+  const int PG = min(NP, P - p0);
   const int t = threadIdx.x;
   const int pl = t >> 4, blk = t & 15, lane = t & 31;
   const bool on = pl < PG;
@@ -817,7 +844,7 @@ __global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int 
   const int by = morton_y(blk), bx = morton_x(blk);
   const int i0 = tr * 16 + 4 * by, j0 = tc * 16 + 4 * bx;
   const int Wm = g.W - 1;
-  float* stage = smem;                          // [255][kKscPitch]
+  float* stage = smem;                          // [255][kPitch]
 
   // resample (translation: 5 x 8 aligned window, pre-scaled by 1/2) and levels 1-2
   const int o = (-(pr.kx + 1)) & 3;
@@ -862,7 +889,7 @@ __global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int 
       for (int b = 0; b < 3; ++b) {
         float val = d[b];
         if (pm & 2u) val = perm_value(a, pr, c, 1, b, tr * 8 + r, tc * 8 + col);
-        if (on) stage[(b * 64 + r * 8 + col) * kKscPitch + pl] = val;
+        if (on) stage[(b * 64 + r * 8 + col) * kPitch + pl] = val;
       }
     }
   float A;
@@ -873,7 +900,7 @@ __global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int 
     for (int b = 0; b < 3; ++b) {
       float val = d[b];
       if (pm & 4u) val = perm_value(a, pr, c, 2, b, tr * 4 + by, tc * 4 + bx);
-      if (on) stage[(192 + b * 16 + by * 4 + bx) * kKscPitch + pl] = val;
+      if (on) stage[(192 + b * 16 + by * 4 + bx) * kPitch + pl] = val;
     }
     A = 0.5f * ((ea + eb) + (ec + ed));
   }
@@ -893,7 +920,7 @@ __global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int 
       const int rr = by >> (lvl - 2), cc = bx >> (lvl - 2);
       if ((pm >> lvl) & 1u) val = perm_value(a, pr, c, lvl, m, tr * (16 >> lvl) + rr, tc * (16 >> lvl) + cc);
       const int kl = (lvl == 3) ? 240 + m * 4 + rr * 2 + cc : 252 + m;
-      if (on) stage[kl * kKscPitch + pl] = val;
+      if (on) stage[kl * kPitch + pl] = val;
     }
     A = 0.5f * ((e0 + e1) + (e2 + e3));
   }
@@ -909,7 +936,7 @@ __global__ void __launch_bounds__(16 * kKscPlanes) k_shift_ksc(ShiftArgs a, int 
     const int k = ksc_global_k(g, kl, tr, tc);                // warp-uniform
     if (k < a.K) {
       float* orow = out + (long long)k * P + p0;
-      const float* srow = stage + kl * kKscPitch;
+      const float* srow = stage + kl * kPitch;
       for (int q = lane; q < PG; q += 32) orow[q] = srow[q];
     }
   }
@@ -1164,15 +1191,19 @@ static size_t shift_smem_bytes(const Geometry& g, int kind) {
 }
 
 template <int KIND, int OUT, int CG>
-static haar_status_t launch_reg(const ShiftArgs& a, int S, cudaStream_t st) {
+static haar_status_t launch_reg(const ShiftArgs& a0, int S, cudaStream_t st) {
+  ShiftArgs a = a0;
   const int nb = a.g.T / 4;
   // shared floats: the group values sA [CG][nb^2 / 16], then (last CTA of a
-  // shift) the tile-mean image and its scratch, each float4-aligned
+  // shift) the tile-mean image and its scratch, each float4-aligned; for
+  // rotations of maps with W + H <= 1536, the two coordinate tables after them
   const size_t sa = ((size_t)CG * nb * nb / 16 + 3) & ~(size_t)3;
   const size_t nt4 = ((size_t)a.g.n_tiles + 3) & ~(size_t)3;
-  const size_t fl = sa + nt4 + (size_t)a.g.n_tiles / 4 + 16;
-  const size_t sm = fl * sizeof(float);
-  auto fr = k_shift_reg<KIND, OUT, CG>;
+  const size_t fl = (sa + nt4 + (size_t)a.g.n_tiles / 4 + 16 + 3) & ~(size_t)3;
+  const bool smt = KIND == KIND_ROTATE && a.g.W + a.g.H <= 1536;
+  const size_t sm = (fl + (smt ? 4 * (size_t)(a.g.W + a.g.H) : 0)) * sizeof(float);
+  a.tab_off = (int)fl;
+  auto fr = smt ? k_shift_reg<KIND, OUT, CG, true> : k_shift_reg<KIND, OUT, CG, false>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_reg)");
@@ -1257,16 +1288,24 @@ bool ksc_eligible(const haar_shift_desc_t& d, const Geometry& g, int S) {
   const long long P = (long long)S * g.C;
   if ((P + kKscPlanes - 1) / kKscPlanes > S) return false;                 // one counter per plane group
   const long long n16 = (long long)(g.H / 16) * (g.W / 16);
-  return ksc_smem_floats(n16) * sizeof(float) <= 200 * 1024;
+  return ksc_smem_floats(n16, kKscPlanes) * sizeof(float) <= 200 * 1024;
+}
+
+// Planes per CTA: 48, or 24 when a 48-plane grid would not fill two CTAs per
+// SM (e.g. the 16 RGB shifts of a 128 x 256 map: 128 tiles) and the plane
+// groups still fit the per-shift counters.
+static int ksc_planes(const Geometry& g16, long long P, int S) {
+  const long long g48 = (P + kKscPlanes - 1) / kKscPlanes, g24 = (P + 23) / 24;
+  return ((long long)g16.n_tiles * g48 < 304 && g24 <= S) ? 24 : kKscPlanes;
 }
 
 size_t ksc_means_floats(const Geometry& g, int S) {
   return (size_t)S * g.C * (size_t)(g.H / 16) * (g.W / 16);
 }
 
-size_t ksc_smem_floats(long long n16) {
-  const long long coarse = (long long)kKscPlanes * ksc_plane_floats(n16);
-  const long long stage = 255LL * kKscPitch;
+size_t ksc_smem_floats(long long n16, int planes) {
+  const long long coarse = (long long)planes * ksc_plane_floats(n16);
+  const long long stage = 255LL * (planes + 1);
   return (size_t)(coarse > stage ? coarse : stage);
 }
 
@@ -1288,15 +1327,18 @@ static haar_status_t launch_ksc(haar_shift_plan_s* p, const float* coeffs_in, in
   a.rows = nullptr;
   a.rtab = nullptr;
   a.rt_stride = 0;
+  a.tab_off = 0;
   a.scale = 1.0f;
   a.u_scale = a.v_scale = 0.0f;
-  const size_t sm = ksc_smem_floats(g.n_tiles) * sizeof(float);
+  const int np = ksc_planes(g, P, S);
+  const size_t sm = ksc_smem_floats(g.n_tiles, np) * sizeof(float);
+  auto fn = (np == 24) ? k_shift_ksc<24> : k_shift_ksc<kKscPlanes>;
   if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_shift_ksc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_ksc)");
   }
-  dim3 grid(g.n_tiles, (unsigned)((P + kKscPlanes - 1) / kKscPlanes));
-  return cuda_check(launch_pdl(k_shift_ksc, grid, dim3(16 * kKscPlanes), sm, st, a, (int)P), "k_shift_ksc launch");
+  dim3 grid(g.n_tiles, (unsigned)((P + np - 1) / np));
+  return cuda_check(launch_pdl(fn, grid, dim3(16 * np), sm, st, a, (int)P), "k_shift_ksc launch");
 }
 
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
@@ -1325,6 +1367,7 @@ haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, 
   a.rows = reinterpret_cast<const float4*>(p->trig);
   a.rtab = reinterpret_cast<const float4*>(p->rtab);
   a.rt_stride = rot_table_float4s(g.H, g.W);
+  a.tab_off = 0;
   a.scale = 1.0f;
   a.u_scale = (float)(g.H / 3.14159265358979323846);
   a.v_scale = (float)(g.W / (2.0 * 3.14159265358979323846));
@@ -1351,6 +1394,7 @@ haar_status_t launch_forward(int H, int W, int batch, const float* maps, float* 
   a.rows = nullptr;
   a.rtab = nullptr;
   a.rt_stride = 0;
+  a.tab_off = 0;
   a.scale = scale;
   a.u_scale = a.v_scale = 0.0f;
   // details are scaled by put(); tile means are stashed unscaled and scaled
