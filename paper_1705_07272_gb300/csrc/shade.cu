@@ -135,10 +135,15 @@ __global__ void __launch_bounds__(256) k_shade_bincsr_f16(const __half* __restri
                                                           const float* __restrict__ L, long long NL,
                                                           float* __restrict__ R) {
   pdl_wait();                                     // inputs come from the previous kernel
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  // CTA = 8 vertices x one shift, the shift fastest across CTAs: a CTA's
+  // gathers all fall in one shift's lighting plane (L1-resident), and the S
+  // CTAs of a vertex block run together, so each stored row they share is
+  // fetched from DRAM once
   const int lane = threadIdx.x & 31;
-  if (warp >= (long long)V * S) return;
-  const int v = (int)(warp / S), s = (int)(warp - (long long)v * S);
+  const long long cta = blockIdx.x;
+  const int s = (int)(cta % S);
+  const int v = (int)(cta / S) * 8 + (threadIdx.x >> 5);
+  if (v >= V) return;
   const int b = __ldg(bin_of + (long long)s * V + v);
   const long long row = ((long long)v * bins + b) * K;
   const int cs = VEC4 ? 4 : C;                              // floats per coefficient
@@ -670,8 +675,7 @@ haar_status_t launch_gcsr_pack(int V, int N, const int32_t* rowptr, const uint16
 haar_status_t launch_shade_bincsr_f16(const __half* vals, const uint32_t* idx, const uint8_t* bin_of,
                                       int V, int bins, int K, int S, int C, const float* L, long long NL,
                                       bool vec4, float* R, cudaStream_t st) {
-  const long long threads = (long long)V * S * 32;
-  const dim3 grid((unsigned)((threads + 255) / 256));
+  const dim3 grid((unsigned)(((long long)V + 7) / 8 * S));
   const cudaError_t e =
       vec4 ? launch_pdl(k_shade_bincsr_f16<true>, grid, dim3(256), 0, st, vals, idx, bin_of, V, bins, K, S, C, L, NL, R)
            : launch_pdl(k_shade_bincsr_f16<false>, grid, dim3(256), 0, st, vals, idx, bin_of, V, bins, K, S, C, L, NL, R);
