@@ -357,17 +357,56 @@ __global__ void __launch_bounds__(256, 2) k_shade_gcsr_f32(const float* __restri
   }
 }
 
+
+// One batch of 4 N entries of the union list (N warp steps, no per-step
+// predicates: entries past the list's end are (row 0, value 0)), the rows
+// of step p + D requested while step p's products issue.  sw = the warp's
+// staged values, myk = lane j's index of entry j of the batch.
+template <int N, int D>
+__device__ __forceinline__ void gcsr48_batch(unsigned long long (&acc)[kGroup][3], const float4* sw, int myk,
+                                             const ulonglong2* La, const unsigned long long* Lb, int es) {
+  typedef unsigned long long u64;
+  ulonglong2 xa[N];
+  u64 xb[N];
+#pragma unroll
+  for (int p = 0; p < D && p < N; ++p) {
+    const int k = __shfl_sync(0xffffffffu, myk, 4 * p + es);
+    xa[p] = __ldg(La + (unsigned)k * 12u);
+    xb[p] = __ldg(Lb + (unsigned)k * 24u);
+  }
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    if (p + D < N) {
+      const int k = __shfl_sync(0xffffffffu, myk, 4 * (p + D) + es);
+      xa[p + D] = __ldg(La + (unsigned)k * 12u);
+      xb[p + D] = __ldg(Lb + (unsigned)k * 24u);
+    }
+    const float4 t = sw[4 * p + es];
+    const u64 tt[4] = {f2_dup(t.x), f2_dup(t.y), f2_dup(t.z), f2_dup(t.w)};
+#pragma unroll
+    for (int v = 0; v < kGroup; ++v) {
+      acc[v][0] = f2_fma(tt[v], xa[p].x, acc[v][0]);
+      acc[v][1] = f2_fma(tt[v], xa[p].y, acc[v][1]);
+      acc[v][2] = f2_fma(tt[v], xb[p], acc[v][2]);
+    }
+  }
+}
+
 // Group-CSR shading for rows of exactly 48 floats (16 shifts x RGB, the c1
-// frame) at 4 CTAs per SM: the same CTA = 4 groups x 2 warps and batch
-// pipeline as k_shade_gcsr_f32, but a row is spread over 8 lanes (lane = 8 e
-// + c: entry slot e of 4, floats 4c..4c+3 and 32+2c..33+2c of the row), so a
-// lane holds 12 paired accumulators (4 vertices x 6 floats) instead of 24 and
-// twice as many warps share each SM to hide the row gathers' latency.
-__global__ void __launch_bounds__(256, 4) k_shade_gcsr48(const float* __restrict__ vals,
-                                                         const uint16_t* __restrict__ idx,
-                                                         const int32_t* __restrict__ gptr, int V,
-                                                         const float* __restrict__ L, int NL,
-                                                         float* __restrict__ R) {
+// frame): the same CTA = 4 groups x 2 warps and batch staging as
+// k_shade_gcsr_f32, but a row is spread over 8 lanes (lane = 8 e + c: entry
+// slot e of 4, floats 4c..4c+3 and 32+2c..33+2c of the row), so a lane holds
+// 12 paired accumulators (4 vertices x 6 floats) instead of 24.  Each batch of
+// 32 entries runs as 8 (or, for the last 16 or fewer, 4) predicate-free warp
+// steps with the rows of step p + 3 in flight while step p's products issue
+// (80 registers, 3 CTAs per SM).
+constexpr int kGcsr48Ahead = 3;
+
+__global__ void __launch_bounds__(256, 3) k_shade_gcsr48(const float* __restrict__ vals,
+                                                           const uint16_t* __restrict__ idx,
+                                                           const int32_t* __restrict__ gptr, int V,
+                                                           const float* __restrict__ L, int NL,
+                                                           float* __restrict__ R) {
   pdl_wait();                                     // inputs come from the previous kernel
   typedef unsigned long long u64;
   __shared__ u64 red[4][8][kGroup][3];
@@ -377,6 +416,8 @@ __global__ void __launch_bounds__(256, 4) k_shade_gcsr48(const float* __restrict
   const int n_groups = (V + kGroup - 1) / kGroup;
   const int es = lane >> 3, c8 = lane & 7;
   const float4* V4 = reinterpret_cast<const float4*>(vals);
+  const ulonglong2* La = reinterpret_cast<const ulonglong2*>(L) + c8;
+  const u64* Lb = reinterpret_cast<const u64*>(L + 32) + c8;
   const int g = blockIdx.x * 4 + gl;
   if (g >= n_groups) return;                      // both warps of a pair leave together
   const int beg = __ldg(gptr + g), end = __ldg(gptr + g + 1);
@@ -412,40 +453,8 @@ __global__ void __launch_bounds__(256, 4) k_shade_gcsr48(const float* __restrict
       nv = ld_stream_f4(V4 + jn);
       if (nk >= NL) { nk = 0; nv = make_float4(0.f, 0.f, 0.f, 0.f); }
     }
-    const int steps = min(8, (je - j0 + 3) >> 2);              // warp-uniform
-    ulonglong2 xa;
-    u64 xb;
-    {
-      const int k = __shfl_sync(0xffffffffu, myk, es);
-      const float* row = L + (unsigned)k * 48u;
-      xa = __ldg(reinterpret_cast<const ulonglong2*>(row) + c8);
-      xb = __ldg(reinterpret_cast<const u64*>(row + 32) + c8);
-    }
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      if (p < steps) {
-        ulonglong2 na;
-        u64 nb;
-        if (p + 1 < steps) {
-          const int k = __shfl_sync(0xffffffffu, myk, 4 * (p + 1) + es);
-          const float* row = L + (unsigned)k * 48u;
-          na = __ldg(reinterpret_cast<const ulonglong2*>(row) + c8);
-          nb = __ldg(reinterpret_cast<const u64*>(row + 32) + c8);
-        }
-        const float4 t = sv[w][4 * p + es];
-        const u64 tt[4] = {f2_dup(t.x), f2_dup(t.y), f2_dup(t.z), f2_dup(t.w)};
-#pragma unroll
-        for (int v = 0; v < kGroup; ++v) {
-          acc[v][0] = f2_fma(tt[v], xa.x, acc[v][0]);
-          acc[v][1] = f2_fma(tt[v], xa.y, acc[v][1]);
-          acc[v][2] = f2_fma(tt[v], xb, acc[v][2]);
-        }
-        if (p + 1 < steps) {
-          xa = na;
-          xb = nb;
-        }
-      }
-    }
+    if (je - j0 > 16) gcsr48_batch<8, kGcsr48Ahead>(acc, sv[w], myk, La, Lb, es);
+    else gcsr48_batch<4, kGcsr48Ahead>(acc, sv[w], myk, La, Lb, es);
   }
   // sum the 4 entry slots (lanes c8, c8 + 8, c8 + 16, c8 + 24), then the pair's halves
 #pragma unroll
