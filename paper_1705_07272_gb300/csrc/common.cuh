@@ -19,7 +19,8 @@ struct ShiftParam {
   float wx0, wx1, wy0, wy1;  // bilinear weights: g = wy0 (wx0 F[i-ky][j-kx] + wx1 F[i-ky][j-kx-1])
                              //                    + wy1 (wx0 F[i-ky-1][j-kx] + wx1 F[i-ky-1][j-kx-1])
   uint32_t perm_mask;        // bit l (1..n): level l is a signed permutation; bit n+1: scaling
-  int pad;
+  int order;                 // translations: record y's `order` is the shift that CTA row y of the
+                             // 8 x 8-block batch kernel takes (shifts grouped by column phase)
   float R[9];                // rotation p' = R p (row-major), float32
   float a_px;                // rotations: a / dphi - 1/2 for R = Ry(a) Rx(b) Ry(c) (picks anchor columns)
   float pad2[2];

@@ -796,6 +796,268 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift
   if (lane == 0) a.counters[s] = 0u;
 }
 
+// ------------------------------------------------------------------ translation, 8 x 8 blocks
+// F32 translations into a k-contiguous layout (batches of many shifts):
+// CTA = one 64 x 64 output tile of one shift, all channels, thread per 8 x 8
+// block of output pixels (64 threads).  Per channel a thread streams the 9
+// source rows of its block's window (3 aligned float4 loads per row, the
+// rows' offsets computed once per thread), lerps each row horizontally and
+// each pair of rows vertically (weights pre-scaled by 1/2, exact), and
+// finishes levels 1-3 of its block in registers: level-1 details leave as
+// one float4 per row and band, level 2 as float2, level 3 as scalars.  The
+// level-3 means of the tile go through shared memory to levels 4-6, and the
+// last CTA of a shift runs the coarse levels.  Against the 4 x 4 block of
+// k_shift_reg, a thread's window loads, row addresses and stores are shared
+// by 4x the outputs, and no level needs a shuffle merge.
+constexpr int kTr8Threads = 64;
+
+template <int O>
+__device__ __forceinline__ void tr8_hlerp(const float4 (&v)[3], float wx0, float wx1, float (&h)[8]) {
+  const float w[12] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y,
+                       v[1].z, v[1].w, v[2].x, v[2].y, v[2].z, v[2].w};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) h[q] = wx0 * w[O + q + 1] + wx1 * w[O + q];
+}
+
+// the 3 float4 of window row `off` (row * W + first aligned column); wrap:
+// the window crosses the last column, each float4 column wraps separately
+__device__ __forceinline__ void tr8_load(const float* __restrict__ F, int off, bool wrap, int Wm,
+                                         float4 (&v)[3]) {
+  if (!wrap) {
+    const float4* p = reinterpret_cast<const float4*>(F + off);
+    v[0] = __ldg(p);
+    v[1] = __ldg(p + 1);
+    v[2] = __ldg(p + 2);
+  } else {
+    const int c = off & Wm, rb = off - c;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) v[m] = __ldg(reinterpret_cast<const float4*>(F + rb + ((c + 4 * m) & Wm)));
+  }
+}
+
+// Signed-permutation levels (dyadic integer shifts): the `cnt` coefficients
+// of row r, columns c0.. of level lvl, every band, taken from the input
+// (kept out of line: the hot path only tests the level's bit).
+__device__ __noinline__ void tr8_perm_row(const ShiftArgs& a, const ShiftParam& pr, int c, int lvl, int r, int c0,
+                                          int cnt, float* __restrict__ ob) {
+  const Geometry& g = a.g;
+  const long long gl = (long long)g.q << (2 * (g.n - lvl));
+  float* p = ob + (long long)r * (g.W >> lvl) + c0;
+  for (int b = 0; b < cnt; ++b)
+    for (int m = 0; m < 3; ++m) p[(1 + m) * gl + b] = perm_value(a, pr, c, lvl, m, r, c0 + b);
+}
+
+// Rows 4u .. 4u + 3 of a channel's 8 x 8 block (source rows 4u + 1 .. 4u + 4
+// at offsets o1..o4; hA holds the horizontally lerped row 4u and leaves with
+// row 4u + 4): level 1 of its two row pairs and level 2 of its two 2 x 2
+// blocks; a2 receives the two level-2 means.
+template <int O>
+__device__ __forceinline__ void tr8_half(const ShiftArgs& a, const ShiftParam& pr, int c, const float* __restrict__ F,
+                                         float* __restrict__ ob, int o1, int o2, int o3, int o4, bool wrap, int u,
+                                         int i0, int j0, float (&hA)[8], float (&a2)[2]) {
+  const Geometry& g = a.g;
+  const int Wm = g.W - 1;
+  const float wx0 = pr.wx0, wx1 = pr.wx1, wy0 = 0.5f * pr.wy0, wy1 = 0.5f * pr.wy1;
+  const long long g1 = (long long)g.q << (2 * (g.n - 1)), g2 = g1 >> 2;
+  const int cols1 = g.W >> 1, cols2 = g.W >> 2;
+  const uint32_t pm = pr.perm_mask;
+  float4 v[3];
+  float hB[8], hC[8];
+  float A1[2][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    tr8_load(F, h ? o3 : o1, wrap, Wm, v);
+    tr8_hlerp<O>(v, wx0, wx1, hB);
+    tr8_load(F, h ? o4 : o2, wrap, Wm, v);
+    tr8_hlerp<O>(v, wx0, wx1, hC);
+    float Dh[4], Dv[4], Dd[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float ea = wy0 * hB[2 * b] + wy1 * hA[2 * b], eb = wy0 * hB[2 * b + 1] + wy1 * hA[2 * b + 1];
+      const float ec = wy0 * hC[2 * b] + wy1 * hB[2 * b], ed = wy0 * hC[2 * b + 1] + wy1 * hB[2 * b + 1];
+      A1[h][b] = (ea + eb) + (ec + ed);
+      Dh[b] = (eb + ed) - (ea + ec);
+      Dv[b] = (ec + ed) - (ea + eb);
+      Dd[b] = (ea + ed) - (eb + ec);
+    }
+    const int r1 = (i0 >> 1) + 2 * u + h, c1 = j0 >> 1;
+    float* p1 = ob + (long long)r1 * cols1 + c1;
+    *reinterpret_cast<float4*>(p1 + g1) = make_float4(Dh[0], Dh[1], Dh[2], Dh[3]);
+    *reinterpret_cast<float4*>(p1 + 2 * g1) = make_float4(Dv[0], Dv[1], Dv[2], Dv[3]);
+    *reinterpret_cast<float4*>(p1 + 3 * g1) = make_float4(Dd[0], Dd[1], Dd[2], Dd[3]);
+    if (pm & 2u) tr8_perm_row(a, pr, c, 1, r1, c1, 4, ob);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) hA[q] = hC[q];
+  }
+  float Dh[2], Dv[2], Dd[2];
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    const float ea = A1[0][2 * w], eb = A1[0][2 * w + 1], ec = A1[1][2 * w], ed = A1[1][2 * w + 1];
+    a2[w] = 0.5f * ((ea + eb) + (ec + ed));
+    Dh[w] = 0.5f * ((eb + ed) - (ea + ec));
+    Dv[w] = 0.5f * ((ec + ed) - (ea + eb));
+    Dd[w] = 0.5f * ((ea + ed) - (eb + ec));
+  }
+  const int r2 = (i0 >> 2) + u, c2 = j0 >> 2;
+  float* p2 = ob + (long long)r2 * cols2 + c2;
+  *reinterpret_cast<float2*>(p2 + g2) = make_float2(Dh[0], Dh[1]);
+  *reinterpret_cast<float2*>(p2 + 2 * g2) = make_float2(Dv[0], Dv[1]);
+  *reinterpret_cast<float2*>(p2 + 3 * g2) = make_float2(Dd[0], Dd[1]);
+  if (pm & 4u) tr8_perm_row(a, pr, c, 2, r2, c2, 2, ob);
+}
+
+// Levels 1-3 of one channel's 8 x 8 block; returns the level-3 mean.
+// ob = the (shift, channel) plane, (i0, j0) the block's first pixel.  The
+// two halves run as a rolled loop: the unrolled block (x 4 column phases)
+// measured slower, bound by instruction fetch.
+template <int O>
+__device__ __forceinline__ float tr8_block(const ShiftArgs& a, const ShiftParam& pr, int c, const float* __restrict__ F,
+                                           float* __restrict__ ob, const int (&off)[9], bool wrap, int i0, int j0) {
+  const Geometry& g = a.g;
+  float4 v[3];
+  float hA[8];
+  tr8_load(F, off[0], wrap, g.W - 1, v);
+  tr8_hlerp<O>(v, pr.wx0, pr.wx1, hA);
+  float a20[2], a21[2];
+#pragma unroll 1
+  for (int u = 0; u < 2; ++u) {
+    float t[2];
+    tr8_half<O>(a, pr, c, F, ob, u ? off[5] : off[1], u ? off[6] : off[2], u ? off[7] : off[3],
+                u ? off[8] : off[4], wrap, u, i0, j0, hA, t);
+    if (u == 0) { a20[0] = t[0]; a20[1] = t[1]; } else { a21[0] = t[0]; a21[1] = t[1]; }
+  }
+  // level 3
+  const float ea = a20[0], eb = a20[1], ec = a21[0], ed = a21[1];
+  const long long g3 = (long long)g.q << (2 * (g.n - 3));
+  const int r3 = i0 >> 3, c3 = j0 >> 3;
+  float* p3 = ob + (long long)r3 * (g.W >> 3) + c3;
+  p3[g3] = 0.5f * ((eb + ed) - (ea + ec));
+  p3[2 * g3] = 0.5f * ((ec + ed) - (ea + eb));
+  p3[3 * g3] = 0.5f * ((ea + ed) - (eb + ec));
+  if (pr.perm_mask & 8u) tr8_perm_row(a, pr, c, 3, r3, c3, 1, ob);
+  return 0.5f * ((ea + eb) + (ec + ed));
+}
+
+// One level (4 <= lvl <= 6) of the tile from the previous level's means in
+// shared memory: work item e = (channel, block row u, block column v) of an
+// nb x nb grid of 2 x 2 blocks (the source grid is 2 nb wide).
+__device__ __forceinline__ void tr8_level(const ShiftArgs& a, const ShiftParam& pr, int s, int lvl, int nb,
+                                          const float* src, float* dst, int tr, int tc) {
+  const Geometry& g = a.g;
+  const long long gl = (long long)g.q << (2 * (g.n - lvl));
+  const int cols = g.W >> lvl;
+  for (int e = threadIdx.x; e < g.C * nb * nb; e += blockDim.x) {
+    const int c = e / (nb * nb), rem = e - c * nb * nb, u = rem / nb, w = rem - u * nb;
+    const float* q = src + c * 4 * nb * nb;
+    const float ea = q[(2 * u) * 2 * nb + 2 * w], eb = q[(2 * u) * 2 * nb + 2 * w + 1];
+    const float ec = q[(2 * u + 1) * 2 * nb + 2 * w], ed = q[(2 * u + 1) * 2 * nb + 2 * w + 1];
+    float d[3] = {0.5f * ((eb + ed) - (ea + ec)), 0.5f * ((ec + ed) - (ea + eb)), 0.5f * ((ea + ed) - (eb + ec))};
+    const int r = ((tr * g.T) >> lvl) + u, col = ((tc * g.T) >> lvl) + w;
+    float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)c * a.st_c;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      float x = d[m];
+      if ((pr.perm_mask >> lvl) & 1u) x = perm_value(a, pr, c, lvl, m, r, col);
+      ob[gl * (1 + m) + (long long)r * cols + col] = x;
+    }
+    dst[c * nb * nb + u * nb + w] = 0.5f * ((ea + eb) + (ec + ed));
+  }
+}
+
+// Shared memory (floats): level-3 means [C][64], level-4 [C][16], level-5
+// [C][4], then (last CTA of a shift) the tile-mean image and its scratch.
+template <int O>
+__device__ __forceinline__ void tr8_channels(const ShiftArgs& a, const ShiftParam& pr, int s, const int (&off)[9],
+                                             bool wrap, int i0, int j0, float* sA3) {
+  const Geometry& g = a.g;
+#pragma unroll 1
+  for (int c = 0; c < g.C; ++c) {
+    const float* F = a.pix + (long long)c * g.N;
+    float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)c * a.st_c;
+    sA3[c * 64 + threadIdx.x] = tr8_block<O>(a, pr, c, F, ob, off, wrap, i0, j0);
+  }
+}
+
+// 72 registers (14 CTAs per SM); 64 or 80 measured slower
+__global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ ShiftParam s_prm;
+  __shared__ int s_last;
+  const Geometry& g = a.g;
+  const int tile = blockIdx.x;
+  const int tr = tile / g.tiles_c, tc = tile - tr * g.tiles_c;
+  pdl_wait();
+  const int s = a.prm[blockIdx.y].order;              // CTA rows run the shifts grouped by column phase
+  if (threadIdx.x == 0) s_prm = a.prm[s];
+  __syncthreads();
+  const ShiftParam& pr = s_prm;          // shared: perm_value and the coarse pass take it by reference
+  // the thread's block: row-major 8 x 8 grid of blocks in the tile
+  const int by = threadIdx.x >> 3, bx = threadIdx.x & 7;
+  const int i0 = tr * g.T + 8 * by, j0 = tc * g.T + 8 * bx;
+  const int Wm = g.W - 1;
+  const int o = (-(pr.kx + 1)) & 3;                       // column phase, the same for every row
+  const int cb = j0 - pr.kx - 1 - o;                      // 16-byte aligned first column
+  int off[9];
+  bool wrap = false;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    int i = i0 - pr.ky - 1 + r, sh = 0;
+    if (g.boundary == HAAR_BOUNDARY_TORUS) {
+      i &= (g.H - 1);
+    } else {
+#pragma unroll 1
+      for (int it = 0; it < 8 && (i < 0 || i >= g.H); ++it) {
+        i = (i < 0) ? -1 - i : 2 * g.H - 1 - i;
+        sh ^= 1;
+      }
+    }
+    const int c = (cb + (sh ? (g.W >> 1) : 0)) & Wm;
+    off[r] = i * g.W + c;
+    wrap |= c + 12 > g.W;
+  }
+  float* sA3 = smem;
+  float* sA4 = sA3 + 64 * g.C;
+  float* sA5 = sA4 + 16 * g.C;
+  float* sA6 = sA5 + 4 * g.C;
+  switch (o) {
+    case 0: tr8_channels<0>(a, pr, s, off, wrap, i0, j0, sA3); break;
+    case 1: tr8_channels<1>(a, pr, s, off, wrap, i0, j0, sA3); break;
+    case 2: tr8_channels<2>(a, pr, s, off, wrap, i0, j0, sA3); break;
+    default: tr8_channels<3>(a, pr, s, off, wrap, i0, j0, sA3); break;
+  }
+  pdl_trigger();
+  __syncthreads();
+  tr8_level(a, pr, s, 4, 4, sA3, sA4, tr, tc);
+  __syncthreads();
+  tr8_level(a, pr, s, 5, 2, sA4, sA5, tr, tc);
+  __syncthreads();
+  tr8_level(a, pr, s, 6, 1, sA5, sA6, tr, tc);
+  __syncthreads();
+  for (int c = threadIdx.x; c < g.C; c += blockDim.x) {
+    if (a.means != nullptr)
+      a.means[((long long)s * g.C + c) * g.n_tiles + tile] = sA6[c];
+    else  // forward transform: stash the tile mean in the coarse region of the output
+      reinterpret_cast<float*>(a.out)[(long long)s * a.st_s + (long long)c * a.st_c + tile] = sA6[c];
+  }
+  if (a.counters == nullptr) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(a.counters + s, 1u);
+    s_last = (t == (unsigned)(g.n_tiles - 1)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  float* img = sA6 + ((g.C + 3) & ~3);
+  float* img2 = img + ((g.n_tiles + 3) & ~3);
+  for (int c = 0; c < g.C; ++c) {
+    for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
+      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
+    coarse_levels<HAAR_OUT_F32>(a, &s_prm, s, c, img, img2);
+  }
+  if (threadIdx.x == 0) a.counters[s] = 0u;
+}
+
 // Coefficient-major translation kernel: one CTA takes a 16 x 16 output tile
 // for a group of up to kKscPlanes (shift, channel) planes, one thread per
 // (plane, 4 x 4 block).  Levels 1-4 of every plane are staged in shared
@@ -1090,7 +1352,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
       p.wx0 = p.wy0 = 1.0f;
       p.wx1 = p.wy1 = 0.0f;
       p.perm_mask = 0u;
-      p.pad = 0;
+      p.order = 0;
       for (int k = 0; k < 9; ++k) p.R[k] = (float)R[k];
       p.a_px = (float)(atan2(sh[w][0], sh[w][1]) * (a.W / (2.0 * 3.14159265358979323846)) - 0.5);
       p.pad2[0] = p.pad2[1] = 0.0f;
@@ -1110,7 +1372,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
     p.wx0 = p.wy0 = 1.0f;
     p.wx1 = p.wy1 = 0.0f;
     p.perm_mask = 0u;
-    p.pad = 0;
+    p.order = 0;
     for (int k = 0; k < 9; ++k) p.R[k] = (k % 4 == 0) ? 1.0f : 0.0f;
     p.a_px = 0.0f;
     p.pad2[0] = p.pad2[1] = 0.0f;
@@ -1147,6 +1409,28 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
     }
     a.prm[s] = p;
     a.counters[s] = 0u;
+  }
+  if (a.kind != HAAR_SHIFT_TRANSLATE) return;
+  // translations: list the shifts grouped by column phase (kx + 1) mod 4 in
+  // the records' `order` fields, so that the batch kernel's co-resident CTAs
+  // mostly run the same one of its four phase-specialised code paths
+  __shared__ int cnt[4];
+  if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < a.S; s += blockDim.x) atomicAdd(&cnt[(-(a.prm[s].kx + 1)) & 3], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int o = 0; o < 4; ++o) {
+      const int c = cnt[o];
+      cnt[o] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
+    const int pos = atomicAdd(&cnt[(-(a.prm[s].kx + 1)) & 3], 1);
+    a.prm[pos].order = s;
   }
 }
 
@@ -1216,8 +1500,29 @@ static haar_status_t launch_reg(const ShiftArgs& a0, int S, cudaStream_t st) {
 // channels; a translation shares only its window addresses, so it takes
 // kRotChannels channels per thread only when that still leaves several
 // waves of CTAs (otherwise one channel per CTA, for parallelism).
+// The 8 x 8-block translation kernel serves F32 batches of many shifts into a
+// k-contiguous, untruncated layout with 16-byte aligned planes.
+static bool tr8_eligible(const ShiftArgs& a, int S) {
+  return a.g.T == 64 && a.st_k == 1 && a.scale == 1.0f && a.K >= a.g.N && a.st_s % 4 == 0 && a.st_c % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(a.out) & 15) == 0 && (long long)a.g.n_tiles * S >= 2432;
+}
+
+static haar_status_t launch_tr8(const ShiftArgs& a, int S, cudaStream_t st) {
+  const size_t fl = 84 * (size_t)a.g.C + 4 + (((size_t)a.g.n_tiles + 3) & ~(size_t)3) + (size_t)a.g.n_tiles / 4 + 16;
+  const size_t sm = ((fl + 3) & ~(size_t)3) * sizeof(float);
+  auto fn = k_shift_tr8;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_tr8)");
+  }
+  return cuda_check(launch_pdl(fn, dim3(a.g.n_tiles, S), dim3(kTr8Threads), sm, st, a), "k_shift_tr8 launch");
+}
+
 template <int KIND, int OUT>
 static haar_status_t launch_k(const ShiftArgs& a, int S, cudaStream_t st) {
+  if constexpr (KIND == KIND_TRANSLATE && OUT == HAAR_OUT_F32) {
+    if (tr8_eligible(a, S)) return launch_tr8(a, S, st);
+  }
   if (a.g.T >= 32) {
     if constexpr (KIND == KIND_COPY) {
       return launch_reg<KIND, OUT, 1>(a, S, st);

@@ -115,6 +115,33 @@ def test_dyadic_shifts_bit_exact(hs, H, W, boundary, layout):
         assert np.array_equal(got[s][:, idx], want), (kx, ky)
 
 
+@pytest.mark.parametrize("boundary", [SPH, TOR])
+@pytest.mark.parametrize("H,W", [(128, 256), (256, 512)])
+def test_dyadic_shifts_bit_exact_batch(hs, H, W, boundary):
+    # enough shifts for the 8 x 8-block batch kernel (>= 2432 tile-shifts):
+    # integer shifts that are multiples of 2^l give signed permutations of
+    # levels <= l, bit-exact, and the other coefficients stay within FP32
+    # rounding of the oracle
+    c = _lighting(2, H, W, 17)
+    base = np.array([[0, 0], [W, 0], [2, 0], [4, 4], [8, 2], [W // 2, H], [16, 2 * H - 16], [6, 10],
+                     [64, 32], [-4, -8], [W - 8, 3 * H // 2 + 8], [32, -64]], dtype=np.float64)
+    S = -(-2432 // ((H // 64) * (W // 64)))
+    cases = np.concatenate([base, np.tile(base, (S // len(base) + 1, 1))])[:max(S, len(base))]
+    got, _ = _run(hs, c, H, W, 0, cases, boundary, 0, 0)
+    per = 2 * H if boundary == SPH else H
+    for s in range(len(base)):
+        kx, ky = cases[s].astype(int)
+        res = osh.dyadic_permutation(c, H, W, int(kx) % W, int(ky) % per, boundary)
+        idx = np.array(sorted(res))
+        want = np.stack([res[k] for k in idx], axis=-1)
+        assert np.array_equal(got[s][:, idx], want), (kx, ky)
+    # repeated shifts give the same bits wherever they sit in the batch
+    for s in range(len(base), len(cases), 37):
+        assert np.array_equal(got[s], got[s % len(base)])
+    ref = osh.haar_shift(c, H, W, osh.TRANSLATE, cases[:len(base)], boundary)
+    assert rel_l2(got[:len(base)], ref, axis=(1, 2)).max() <= 1e-5
+
+
 @pytest.mark.parametrize("H,W", [(2, 2), (2, 4), (4, 4), (4, 8), (8, 16)])
 def test_exhaustive_operator_matrices(hs, H, W):
     # P13: M = Haar . S . Haar^-1 for all integer shifts and a 1/8 grid
