@@ -708,30 +708,32 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
     long long step = 0;
     long long it = 0;                         // tiles done (phase of the reduction barrier)
     bool ok = true;
-    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++it) {
+    // this warp's column group of a tile's folded output layer (the tile's
+    // rows span at most two shifts)
+    auto load_weff = [&](long long t) {
       const long long row0 = t * BM;
-      // ---- this warp's column group of the tile's folded output layer (the
-      // tile's rows span at most two shifts)
       const int s_lo = (int)(row0 / f.V);
       const int s_hi = (int)((row0 + BM - 1 < f.rows ? row0 + BM - 1 : f.rows - 1) / f.V);
-      {
-        __syncwarp();
-        for (int i = lane; i < 2 * F_COLS; i += 32) {
-          // local column j = 16 kb + m is layer column 64 kb + 16 cg + m
-          const int k = i / F_COLS, j = i - k * F_COLS;
-          const int col = 64 * (j >> 4) + 16 * cg + (j & 15);
-          const float* W = f.weff + ((long long)(k ? s_hi : s_lo) * WIDTH + col) * f.C;
-          float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
-          w4.x = W[0];
-          if (f.C > 1) w4.y = W[1];
-          if (f.C > 2) w4.z = W[2];
-          if (f.C > 3) w4.w = W[3];
-          *reinterpret_cast<float4*>(&sweff[wid][k][j][0]) = w4;
-        }
-        __syncwarp();
+      __syncwarp();
+      for (int i = lane; i < 2 * F_COLS; i += 32) {
+        // local column j = 16 kb + m is layer column 64 kb + 16 cg + m
+        const int k = i / F_COLS, j = i - k * F_COLS;
+        const int col = 64 * (j >> 4) + 16 * cg + (j & 15);
+        const float* W = f.weff + ((long long)(k ? s_hi : s_lo) * WIDTH + col) * f.C;
+        float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        w4.x = W[0];
+        if (f.C > 1) w4.y = W[1];
+        if (f.C > 2) w4.z = W[2];
+        if (f.C > 3) w4.w = W[3];
+        *reinterpret_cast<float4*>(&sweff[wid][k][j][0]) = w4;
       }
-      // ---- encode F_RPW rows per warp: row info first, then many independent
-      // loads per lane (lanes sweep (row, chunk) pairs)
+      __syncwarp();
+    };
+    // encode F_RPW rows of a tile per warp into the activation buffer (row
+    // info first, then many independent loads per lane: lanes sweep (row,
+    // chunk) pairs), then release its 5 k-blocks to the MMA warp
+    auto encode = [&](long long t) {
+      const long long row0 = t * BM;
       const int r0 = wid * F_RPW;
       if (lane < F_RPW) {
         const long long row = row0 + r0 + lane;
@@ -785,6 +787,14 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       __syncwarp();
       if (lane == 0)
         for (int j = 0; j < 5; ++j) mbar_arrive(smem_u32(&bars.kready[j]));
+    };
+    if (blockIdx.x < n_tiles) {
+      load_weff(blockIdx.x);
+      encode(blockIdx.x);
+    }
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++it) {
+      const long long row0 = t * BM;
+      const int s_lo = (int)(row0 / f.V);
       // ---- layers
       const int r = q * 32 + lane;
       const long long row = row0 + r;
@@ -792,6 +802,10 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
       for (int l = 0; l < 4; ++l, ++step) {
         if (!mbar_wait(smem_u32(&bars.tfull), (uint32_t)(step & 1), status, abort_flag)) { ok = false; break; }
         fence_after();
+        // the last layer's MMAs have read the activation buffer: encode the
+        // next tile now, so that its first layer runs on the tensor cores
+        // while this epilogue computes the tile's radiance
+        if (l == 3 && t + gridDim.x < n_tiles) encode(t + gridDim.x);
         const float* bias = (l < 3) ? sbias[l] : sbias3;
         float acc_c[4] = {0.f, 0.f, 0.f, 0.f};
         int s = 0;
@@ -855,6 +869,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap w0, const __grid_constant__ CUte
           }
         }
       }
+      if (ok && t + gridDim.x < n_tiles) load_weff(t + gridDim.x);   // after this tile's last use of sweff
     }
   }
   fence_before();
