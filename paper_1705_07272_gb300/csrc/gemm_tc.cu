@@ -38,9 +38,37 @@ struct __align__(8) Bars {
   int abort_flag;
 };
 
+// A CTA's work: `rounds` whole vertex tiles (blockIdx.x + i gridDim.x), then,
+// when the tiles do not divide evenly over the CTAs, its part of one of the
+// remaining tiles, each split into tail_p column slices of N / tail_p (so the
+// last round costs 1 / tail_p of a tile instead of one whole tile on a few
+// CTAs).  part < 0: all N columns.
+struct DenseWork {
+  int tile, part;
+};
+__device__ __forceinline__ bool dense_work(int i, int n_tiles, int rounds, int tail_p, DenseWork& w) {
+  if (tail_p <= 1) {
+    w.tile = blockIdx.x + i * gridDim.x;
+    w.part = -1;
+    return w.tile < n_tiles;
+  }
+  if (i < rounds) {
+    w.tile = blockIdx.x + i * gridDim.x;
+    w.part = -1;
+    return true;
+  }
+  if (i == rounds && (int)blockIdx.x < (n_tiles - rounds * (int)gridDim.x) * tail_p) {
+    w.tile = rounds * gridDim.x + blockIdx.x / tail_p;
+    w.part = blockIdx.x % tail_p;
+    return true;
+  }
+  return false;
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
 k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
-             const __grid_constant__ CUtensorMap mapBl, int V, int K, int N, int STAGES,
+             const __grid_constant__ CUtensorMap mapBl, const __grid_constant__ CUtensorMap mapBhT,
+             const __grid_constant__ CUtensorMap mapBlT, int V, int K, int N, int STAGES, int tail_p,
              float* __restrict__ R, int* status, int pf_dist) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ Bars bars;
@@ -51,6 +79,9 @@ k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
   const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)N * BK * 2;
   const uint32_t stage_bytes = a_bytes + 2 * b_bytes;
   const int n_tiles = (V + BM - 1) / BM;
+  const int rounds = n_tiles / (int)gridDim.x;
+  const int NT = N / (tail_p > 1 ? tail_p : 1);           // columns of a tail slice
+  const uint32_t bt_bytes = (uint32_t)NT * BK * 2;
   const int kblocks = K / BK;
   volatile int* abort_flag = &bars.abort_flag;
 
@@ -92,24 +123,34 @@ k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       // the transport tile of the k-block kPrefetchA blocks ahead heads for L2
       // (it streams from HBM; the lighting tiles stay in L2), so the ring's
       // stages wait on L2 rather than on DRAM latency
-      int pf_tile = blockIdx.x, pf_kb = 0;
-      for (int i = 0; i < pf_dist && pf_tile < n_tiles; ++i) {
-        tma_prefetch_2d(&mapA, pf_kb * BK, pf_tile * BM);
-        if (++pf_kb == kblocks) { pf_kb = 0; pf_tile += gridDim.x; }
-      }
-      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      int pf_i = 0, pf_kb = 0;
+      DenseWork pw;
+      bool pf_on = pf_dist > 0 && dense_work(0, n_tiles, rounds, tail_p, pw);
+      auto pf_step = [&]() {
+        tma_prefetch_2d(&mapA, pf_kb * BK, pw.tile * BM);
+        if (++pf_kb == kblocks) {
+          pf_kb = 0;
+          pf_on = dense_work(++pf_i, n_tiles, rounds, tail_p, pw);
+        }
+      };
+      for (int i = 0; i < pf_dist && pf_on; ++i) pf_step();
+      DenseWork w;
+      for (int wi = 0; ok && dense_work(wi, n_tiles, rounds, tail_p, w); ++wi) {
+        const bool tail = w.part >= 0;
         for (int kb = 0; kb < kblocks; ++kb) {
-          if (pf_dist > 0 && pf_tile < n_tiles) {
-            tma_prefetch_2d(&mapA, pf_kb * BK, pf_tile * BM);
-            if (++pf_kb == kblocks) { pf_kb = 0; pf_tile += gridDim.x; }
-          }
+          if (pf_on) pf_step();
           if (!mbar_wait(smem_u32(&bars.empty[stage]), phase ^ 1u, status, abort_flag)) { ok = false; break; }
           const uint32_t sa = base + stage * stage_bytes;
           const uint32_t fb = smem_u32(&bars.full[stage]);
-          mbar_arrive_tx(fb, stage_bytes);
-          tma_load_2d(sa, &mapA, kb * BK, tile * BM, fb);
-          tma_load_2d(sa + a_bytes, &mapBh, kb * BK, 0, fb);
-          tma_load_2d(sa + a_bytes + b_bytes, &mapBl, kb * BK, 0, fb);
+          mbar_arrive_tx(fb, a_bytes + 2 * (tail ? bt_bytes : b_bytes));
+          tma_load_2d(sa, &mapA, kb * BK, w.tile * BM, fb);
+          if (tail) {
+            tma_load_2d(sa + a_bytes, &mapBhT, kb * BK, w.part * NT, fb);
+            tma_load_2d(sa + a_bytes + b_bytes, &mapBlT, kb * BK, w.part * NT, fb);
+          } else {
+            tma_load_2d(sa + a_bytes, &mapBh, kb * BK, 0, fb);
+            tma_load_2d(sa + a_bytes + b_bytes, &mapBl, kb * BK, 0, fb);
+          }
           issued[stage] = 1;
           issued_phase[stage] = phase;
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -126,12 +167,14 @@ k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(BM, N);
+      const uint32_t idesc_full = make_idesc(BM, N), idesc_tail = make_idesc(BM, NT);
       int stage = 0;
       uint32_t phase = 0;
       int it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+      DenseWork w;
+      for (; ok && dense_work(it, n_tiles, rounds, tail_p, w); ++it) {
+        const uint32_t idesc = w.part >= 0 ? idesc_tail : idesc_full;
         const int acc = it & 1;
         const uint32_t accp = (uint32_t)((it >> 1) & 1);
         if (!mbar_wait(smem_u32(&bars.tempty[acc]), accp ^ 1u, status, abort_flag)) { ok = false; break; }
@@ -166,18 +209,20 @@ k_dense_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     const int quarter = warp & 3;
     const int row_in_tile = quarter * 32 + lane;
     int it = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+    DenseWork w;
+    for (; dense_work(it, n_tiles, rounds, tail_p, w); ++it) {
       const int acc = it & 1;
       const uint32_t accp = (uint32_t)((it >> 1) & 1);
       if (!mbar_wait(smem_u32(&bars.tfull[acc]), accp, status, abort_flag)) break;
       fence_after();
-      const long long row = (long long)tile * BM + row_in_tile;
+      const long long row = (long long)w.tile * BM + row_in_tile;
       const uint32_t t_row = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256);
-      for (int c0 = 0; c0 < N; c0 += 16) {
+      const int ncols = w.part >= 0 ? NT : N, col0 = w.part >= 0 ? w.part * NT : 0;
+      for (int c0 = 0; c0 < ncols; c0 += 16) {
         float v[16];
         tmem_ld16(t_row + (uint32_t)c0, v);
         if (row < V) {
-          float4* dst = reinterpret_cast<float4*>(R + row * N + c0);
+          float4* dst = reinterpret_cast<float4*>(R + row * N + col0 + c0);
           dst[0] = make_float4(v[0], v[1], v[2], v[3]);
           dst[1] = make_float4(v[4], v[5], v[6], v[7]);
           dst[2] = make_float4(v[8], v[9], v[10], v[11]);
@@ -205,14 +250,26 @@ haar_status_t launch_shade_dense_bf16_tc(const __nv_bfloat16* T, int V, int K, c
   using namespace tc;
   if (K % BK != 0 || ncols % 16 != 0 || ncols < 16 || ncols > 256)
     return set_error(HAAR_ERR_UNSUPPORTED, "dense bf16 contraction: K %% 64 == 0 and 16 <= S*C <= 256, S*C %% 16 == 0");
-  CUtensorMap mA, mBh, mBl;
-  if (!encode_2d(&mA, T, (uint64_t)K, (uint64_t)V, BK, BM) ||
-      !encode_2d(&mBh, Lhi, (uint64_t)K, (uint64_t)ncols, BK, (uint32_t)ncols) ||
-      !encode_2d(&mBl, Llo, (uint64_t)K, (uint64_t)ncols, BK, (uint32_t)ncols))
-    return set_error(HAAR_ERR_CUDA, "dense bf16 contraction: cuTensorMapEncodeTiled failed");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the tiles left after whole rounds over the CTAs are split into the most
+  // column slices (multiples of 16 columns) that still give each CTA at most one
+  const int n_tiles_h = (V + BM - 1) / BM;
+  const int grid_h = n_tiles_h < sms ? n_tiles_h : sms;
+  const int rem = n_tiles_h % grid_h;
+  int tail_p = 1;
+  if (rem > 0)
+    for (int p = 2; p <= ncols / 16; ++p)
+      if (ncols % (16 * p) == 0 && rem * p <= grid_h) tail_p = p;
+  CUtensorMap mA, mBh, mBl, mBhT, mBlT;
+  const uint32_t nt = (uint32_t)(ncols / tail_p);
+  if (!encode_2d(&mA, T, (uint64_t)K, (uint64_t)V, BK, BM) ||
+      !encode_2d(&mBh, Lhi, (uint64_t)K, (uint64_t)ncols, BK, (uint32_t)ncols) ||
+      !encode_2d(&mBl, Llo, (uint64_t)K, (uint64_t)ncols, BK, (uint32_t)ncols) ||
+      !encode_2d(&mBhT, Lhi, (uint64_t)K, (uint64_t)ncols, BK, nt) ||
+      !encode_2d(&mBlT, Llo, (uint64_t)K, (uint64_t)ncols, BK, nt))
+    return set_error(HAAR_ERR_CUDA, "dense bf16 contraction: cuTensorMapEncodeTiled failed");
   const int n_tiles = (V + BM - 1) / BM;
   const int grid = n_tiles < sms ? n_tiles : sms;
   const size_t stage_bytes = BM * BK * 2 + 2 * (size_t)ncols * BK * 2;
@@ -221,8 +278,8 @@ haar_status_t launch_shade_dense_bf16_tc(const __nv_bfloat16* T, int V, int K, c
   const size_t smem = (size_t)stages * stage_bytes + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_dense_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_dense_bf16)");
-  return cuda_check(launch_pdl(k_dense_bf16, dim3(grid), dim3(THREADS), smem, st, mA, mBh, mBl, V, K, ncols, stages,
-                              R, status, kPrefetchA),
+  return cuda_check(launch_pdl(k_dense_bf16, dim3(grid), dim3(THREADS), smem, st, mA, mBh, mBl, mBhT, mBlT, V, K,
+                              ncols, stages, tail_p, R, status, kPrefetchA),
                     "k_dense_bf16 launch");
 }
 

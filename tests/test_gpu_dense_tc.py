@@ -51,7 +51,10 @@ def _acc_tol(K):
 
 
 @pytest.mark.parametrize("V,K,S,C", [(300, 128, 16, 3), (128, 64, 1, 16), (1000, 4096, 64, 3),
-                                     (4099, 1024, 32, 8), (77, 256, 16, 16)])
+                                     (4099, 1024, 32, 8), (77, 256, 16, 16),
+                                     # more 128-row tiles than the GB300's 152 SMs with a
+                                     # remainder: the leftover tiles run as column slices
+                                     (128 * 160 + 40, 256, 16, 3), (128 * 162, 128, 64, 3)])
 def test_tensor_core_contraction_matches_fp64(hs, V, K, S, C):
     got, ref = _contract(hs, V, K, S, C, V + K)
     assert got.shape == ref.shape
