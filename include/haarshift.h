@@ -124,7 +124,12 @@ typedef struct {
 
 /* Create a plan: validates the descriptor and allocates its device workspace
  * (pixel map C*H*W floats, per-shift tables and counters, shade_batch's
- * lighting buffer) on the current device.  *out receives the plan. */
+ * lighting buffer) on the current device.  Translation plans with float32
+ * SCK output of all N coefficients, H >= 64 and max_shifts * (H/64)(W/64) >=
+ * 2432 also hold the map extended by one period of rows plus 65 and by 68
+ * columns (C*(2H+65)*(W+68) floats for SPHERE, C*(H+65)*(W+68) for TORUS),
+ * from which their batch kernel stages each tile's window by TMA.  *out
+ * receives the plan. */
 HAAR_API haar_status_t haar_shift_plan(const haar_shift_desc_t* desc, haar_shift_plan_t* out);
 
 /* Release a plan and its workspace (synchronises the device first). */

@@ -50,6 +50,7 @@ static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 static void free_plan(haar_shift_plan_s* p) {
   if (!p) return;
   cudaFree(p->pix);
+  cudaFree(p->pixE);
   cudaFree(p->trig);
   cudaFree(p->rtab);
   cudaFree(p->prm);
@@ -127,6 +128,11 @@ haar_status_t haar_shift_plan(const haar_shift_desc_t* d, haar_shift_plan_t* out
       p->light_elems * out_elem_bytes(d->out_type) * (d->out_type == HAAR_OUT_BF16_HILO ? 2 : 1);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&p->pix, sizeof(float) * pix_floats(d->kind, g.H, g.W, g.C));
+  if (e == cudaSuccess && tr8_tma_plan(*d, g, p->K, (int)S)) {
+    p->pixE_H = ((d->boundary == HAAR_BOUNDARY_SPHERE) ? 2 * g.H : g.H) + 65;
+    p->pixE_W = g.W + 68;
+    e = cudaMalloc(&p->pixE, sizeof(float) * (size_t)g.C * p->pixE_H * p->pixE_W);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->trig, sizeof(float) * trig_floats(g.H, g.W));
   if (e == cudaSuccess && (d->kind == HAAR_SHIFT_ROTATE || d->kind == HAAR_SHIFT_ROTATE_EULER))
     e = cudaMalloc(&p->rtab, sizeof(float4) * rot_table_float4s(g.H, g.W) * S);
@@ -195,7 +201,7 @@ haar_status_t haar_shift(haar_shift_plan_t p, const float* cin, const double* pa
   haar_status_t r = check_shift_args(p, cin, params, S, out, "haar_shift");
   if (r != HAAR_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  r = launch_setup(p, cin, params, S, st);
+  r = launch_setup(p, cin, params, out, S, st);
   if (r != HAAR_OK) return r;
   if (p->desc.kind == HAAR_SHIFT_ROTATE_CHAIN) return launch_chain(p, params, S, out, st);
   return launch_shift(p, cin, S, out, st);
@@ -302,7 +308,7 @@ haar_status_t shade_batch(haar_shift_plan_t p, const float* cin, const double* p
   if (r != HAAR_OK) return r;
   if (t == nullptr || R == nullptr) return set_error(HAAR_ERR_INVALID_ARG, "shade_batch: null argument");
   cudaStream_t st = (cudaStream_t)stream;
-  r = launch_setup(p, cin, params, S, st);
+  r = launch_setup(p, cin, params, p->light, S, st);
   if (r != HAAR_OK) return r;
   r = (p->desc.kind == HAAR_SHIFT_ROTATE_CHAIN) ? launch_chain(p, params, S, p->light, st)
                                                 : launch_shift(p, cin, S, p->light, st);

@@ -71,6 +71,10 @@ struct haar_shift_plan_s {
   int device;
   // workspace (device)
   float* pix;                // [C][H][W] pixel map synthesised per launch
+  float* pixE;               // translation batches: the map extended to [C][pixE_H][pixE_W] (rows past the
+                             // poles mirrored half a turn, one period plus a window's rows; columns wrapped
+                             // plus a window's width), so that every tile's source window is one TMA box
+  int pixE_H, pixE_W;
   float* trig;               // rotation tables of the map: see trig_floats()
   float* rtab;               // rotation kinds: per-rotation tables [max_shifts][rot_table_float4s] float4
   hs::ShiftParam* prm;       // [max_shifts]
@@ -187,7 +191,9 @@ haar_status_t cuda_check(cudaError_t e, const char* what);
 bool injected(const char* entry);
 
 // launchers (shift.cu)
-haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const double* params,
+// translation plans whose batches run the 8 x 8-block kernel from the extended map
+bool tr8_tma_plan(const haar_shift_desc_t& d, const Geometry& g, int K, int max_shifts);
+haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const double* params, const void* out,
                            int S, cudaStream_t st);
 haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, void* out,
                            cudaStream_t st);

@@ -121,7 +121,7 @@ extern "C" haar_status_t haar_shift_noalloc(const haar_shift_desc_t* d, const fl
   cudaStream_t st = (cudaStream_t)stream;
   haar_status_t r = HAAR_OK;
   if (d->kind != HAAR_SHIFT_TRANSLATE) r = launch_trig(&p, st);     // tables of this call's map
-  if (r == HAAR_OK) r = launch_setup(&p, cin, params, S, st);        // also zeroes the tile counters
+  if (r == HAAR_OK) r = launch_setup(&p, cin, params, out, S, st);   // also zeroes the tile counters
   if (r == HAAR_OK) r = launch_shift(&p, cin, S, out, st);
   return r;
 }

@@ -15,9 +15,11 @@
 // every level follows from the previous one, O(N) in total).
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "rotcoord.cuh"
+#include "tc.cuh"
 
 namespace hs {
 
@@ -44,6 +46,9 @@ struct ShiftArgs {
   int tab_off;            // rotations, tables in shared memory: their offset in floats
   float scale;
   float u_scale, v_scale; // H/pi, W/(2 pi)
+  const float* pixE = nullptr;   // translation batches: the extended map (see haar_shift_plan_s::pixE)
+  int HE = 0, WE = 0;
+  int* status = nullptr;         // device status word (bounded waits)
 };
 
 // The two row taps of a rotated sample as texel offsets into the interleaved
@@ -821,9 +826,15 @@ __device__ __forceinline__ void tr8_hlerp(const float4 (&v)[3], float wx0, float
 
 // the 3 float4 of window row `off` (row * W + first aligned column); wrap:
 // the window crosses the last column, each float4 column wraps separately
+template <bool SM = false>
 __device__ __forceinline__ void tr8_load(const float* __restrict__ F, int off, bool wrap, int Wm,
                                          float4 (&v)[3]) {
-  if (!wrap) {
+  if (SM) {                                       // the window staged in shared memory
+    const float4* p = reinterpret_cast<const float4*>(F + off);
+    v[0] = p[0];
+    v[1] = p[1];
+    v[2] = p[2];
+  } else if (!wrap) {
     const float4* p = reinterpret_cast<const float4*>(F + off);
     v[0] = __ldg(p);
     v[1] = __ldg(p + 1);
@@ -851,7 +862,7 @@ __device__ __noinline__ void tr8_perm_row(const ShiftArgs& a, const ShiftParam& 
 // at offsets o1..o4; hA holds the horizontally lerped row 4u and leaves with
 // row 4u + 4): level 1 of its two row pairs and level 2 of its two 2 x 2
 // blocks; a2 receives the two level-2 means.
-template <int O>
+template <int O, bool SM>
 __device__ __forceinline__ void tr8_half(const ShiftArgs& a, const ShiftParam& pr, int c, const float* __restrict__ F,
                                          float* __restrict__ ob, int o1, int o2, int o3, int o4, bool wrap, int u,
                                          int i0, int j0, float (&hA)[8], float (&a2)[2]) {
@@ -866,9 +877,9 @@ __device__ __forceinline__ void tr8_half(const ShiftArgs& a, const ShiftParam& p
   float A1[2][4];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    tr8_load(F, h ? o3 : o1, wrap, Wm, v);
+    tr8_load<SM>(F, h ? o3 : o1, wrap, Wm, v);
     tr8_hlerp<O>(v, wx0, wx1, hB);
-    tr8_load(F, h ? o4 : o2, wrap, Wm, v);
+    tr8_load<SM>(F, h ? o4 : o2, wrap, Wm, v);
     tr8_hlerp<O>(v, wx0, wx1, hC);
     float Dh[4], Dv[4], Dd[4];
 #pragma unroll
@@ -910,19 +921,19 @@ __device__ __forceinline__ void tr8_half(const ShiftArgs& a, const ShiftParam& p
 // ob = the (shift, channel) plane, (i0, j0) the block's first pixel.  The
 // two halves run as a rolled loop: the unrolled block (x 4 column phases)
 // measured slower, bound by instruction fetch.
-template <int O>
+template <int O, bool SM = false>
 __device__ __forceinline__ float tr8_block(const ShiftArgs& a, const ShiftParam& pr, int c, const float* __restrict__ F,
                                            float* __restrict__ ob, const int (&off)[9], bool wrap, int i0, int j0) {
   const Geometry& g = a.g;
   float4 v[3];
   float hA[8];
-  tr8_load(F, off[0], wrap, g.W - 1, v);
+  tr8_load<SM>(F, off[0], wrap, g.W - 1, v);
   tr8_hlerp<O>(v, pr.wx0, pr.wx1, hA);
   float a20[2], a21[2];
 #pragma unroll 1
   for (int u = 0; u < 2; ++u) {
     float t[2];
-    tr8_half<O>(a, pr, c, F, ob, u ? off[5] : off[1], u ? off[6] : off[2], u ? off[7] : off[3],
+    tr8_half<O, SM>(a, pr, c, F, ob, u ? off[5] : off[1], u ? off[6] : off[2], u ? off[7] : off[3],
                 u ? off[8] : off[4], wrap, u, i0, j0, hA, t);
     if (u == 0) { a20[0] = t[0]; a20[1] = t[1]; } else { a21[0] = t[0]; a21[1] = t[1]; }
   }
@@ -978,8 +989,60 @@ __device__ __forceinline__ void tr8_channels(const ShiftArgs& a, const ShiftPara
   }
 }
 
+// The TMA-fed form: the tile's source window of every channel (65 rows x 68
+// columns of the extended map, one box) arrives in shared memory by a TMA
+// load, two channels' windows in flight; the threads read their block rows
+// there (offsets off[r] within the window).
+constexpr int kTr8WinRows = 65, kTr8WinCols = 68;
+// one window per CTA (the next channel's copy issued once the current one is
+// read): 17.8 KB of shared memory, 12 CTAs per SM; two windows in flight
+// (35.6 KB, 6 CTAs per SM) measured slower (0.498 against 0.418 ms for 4096
+// shifts of RGB 128x256), as did the direct loads (0.439 ms)
+constexpr int kTr8Windows = 1;
+constexpr int kTr8WinFloats = 4448;              // 65 x 68 rounded up to a 128-byte multiple
+constexpr unsigned long long kTr8WaitNs = 2000000000ull;
+
+// bounded wait on a window's barrier; false (status set) on expiry
+__device__ __forceinline__ bool tr8_wait(uint32_t bar, uint32_t parity, int* status) {
+  if (tc::mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = tc::gtimer();
+  while (!tc::mbar_try(bar, parity))
+    if (tc::gtimer() - t0 > kTr8WaitNs) {
+      if (status != nullptr) atomicOr(status, 1 << HAAR_ERR_TIMEOUT);
+      return false;
+    }
+  return true;
+}
+
+template <int O, int NB>
+__device__ __forceinline__ void tr8_channels_tma(const ShiftArgs& a, const ShiftParam& pr, int s, const int (&off)[9],
+                                                 int i0, int j0, float* sA3, float* win, uint64_t* wbar,
+                                                 int* wissued, int* wdone, const CUtensorMap* mapP, int xw, int yw,
+                                                 int* s_fail) {
+  const Geometry& g = a.g;
+#pragma unroll 1
+  for (int c = 0; c < g.C; ++c) {
+    const int b = c % NB;
+    float* w = win + b * kTr8WinFloats;
+    if (*s_fail == 0 && !tr8_wait(tc::smem_u32(&wbar[b]), (uint32_t)(wdone[b] & 1), a.status)) *s_fail = 1;
+    __syncthreads();
+    const bool ok = *s_fail == 0;
+    if (threadIdx.x == 0 && ok) ++wdone[b];
+    float* ob = reinterpret_cast<float*>(a.out) + (long long)s * a.st_s + (long long)c * a.st_c;
+    if (ok) sA3[c * 64 + threadIdx.x] = tr8_block<O, true>(a, pr, c, w, ob, off, false, i0, j0);
+    __syncthreads();                                // every thread is done with this window
+    if (threadIdx.x == 0 && ok && c + NB < g.C) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc::mbar_arrive_tx(tc::smem_u32(&wbar[b]), kTr8WinRows * kTr8WinCols * 4);
+      tc::tma_load_3d(tc::smem_u32(w), mapP, xw, yw, c + NB, tc::smem_u32(&wbar[b]));
+      ++wissued[b];
+    }
+  }
+}
+
 // 72 registers (14 CTAs per SM); 64 or 80 measured slower
-__global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a) {
+template <bool TMA, int NB>
+__global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, const __grid_constant__ CUtensorMap mapP) {
   extern __shared__ __align__(16) float smem[];
   __shared__ ShiftParam s_prm;
   __shared__ int s_last;
@@ -1000,7 +1063,7 @@ __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a) {
   int off[9];
   bool wrap = false;
 #pragma unroll
-  for (int r = 0; r < 9; ++r) {
+  for (int r = 0; r < 9 && !TMA; ++r) {
     int i = i0 - pr.ky - 1 + r, sh = 0;
     if (g.boundary == HAAR_BOUNDARY_TORUS) {
       i &= (g.H - 1);
@@ -1015,15 +1078,60 @@ __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a) {
     off[r] = i * g.W + c;
     wrap |= c + 12 > g.W;
   }
-  float* sA3 = smem;
+  // TMA: two windows at a 128-byte aligned start (the launch adds 128 bytes)
+  float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+  float* sA3 = TMA ? win + NB * kTr8WinFloats : smem;
   float* sA4 = sA3 + 64 * g.C;
   float* sA5 = sA4 + 16 * g.C;
   float* sA6 = sA5 + 4 * g.C;
-  switch (o) {
-    case 0: tr8_channels<0>(a, pr, s, off, wrap, i0, j0, sA3); break;
-    case 1: tr8_channels<1>(a, pr, s, off, wrap, i0, j0, sA3); break;
-    case 2: tr8_channels<2>(a, pr, s, off, wrap, i0, j0, sA3); break;
-    default: tr8_channels<3>(a, pr, s, off, wrap, i0, j0, sA3); break;
+  if (TMA) {
+    __shared__ uint64_t wbar[2];
+    __shared__ int s_fail, wissued[2], wdone[2];
+    // the tile's window: rows from tile row - ky - 1 (one period, so in [0, per)),
+    // columns from the aligned first column (wrapped, so in [0, W))
+    const int per = (g.boundary == HAAR_BOUNDARY_SPHERE) ? 2 * g.H : g.H;
+    int yw = (tr * g.T - pr.ky - 1) % per;
+    if (yw < 0) yw += per;
+    const int xw = (tc * g.T - pr.kx - 1 - o) & Wm;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) off[r] = (8 * by + r) * kTr8WinCols + 8 * bx;
+    if (threadIdx.x == 0) {
+      s_fail = 0;
+      wdone[0] = wdone[1] = 0;
+      wissued[0] = wissued[1] = 0;
+      tc::mbar_init(tc::smem_u32(&wbar[0]), 1);
+      tc::mbar_init(tc::smem_u32(&wbar[1]), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      for (int c = 0; c < NB && c < g.C; ++c) {
+        tc::mbar_arrive_tx(tc::smem_u32(&wbar[c]), kTr8WinRows * kTr8WinCols * 4);
+        tc::tma_load_3d(tc::smem_u32(win + c * kTr8WinFloats), &mapP, xw, yw, c, tc::smem_u32(&wbar[c]));
+        wissued[c] = 1;
+      }
+    }
+    __syncthreads();
+    switch (o) {
+      case 0: tr8_channels_tma<0, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
+      case 1: tr8_channels_tma<1, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
+      case 2: tr8_channels_tma<2, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
+      default: tr8_channels_tma<3, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
+    }
+    if (s_fail) {
+      // a window never arrived: let any copy still in flight land (bounded)
+      // before the CTA's shared memory is released, then leave (the status
+      // word says why)
+      if (threadIdx.x == 0)
+        for (int b2 = 0; b2 < NB; ++b2)
+          if (wissued[b2] > wdone[b2]) tr8_wait(tc::smem_u32(&wbar[b2]), (uint32_t)(wdone[b2] & 1), nullptr);
+      __syncthreads();
+      return;
+    }
+  } else {
+    switch (o) {
+      case 0: tr8_channels<0>(a, pr, s, off, wrap, i0, j0, sA3); break;
+      case 1: tr8_channels<1>(a, pr, s, off, wrap, i0, j0, sA3); break;
+      case 2: tr8_channels<2>(a, pr, s, off, wrap, i0, j0, sA3); break;
+      default: tr8_channels<3>(a, pr, s, off, wrap, i0, j0, sA3); break;
+    }
   }
   pdl_trigger();
   __syncthreads();
@@ -1258,6 +1366,8 @@ struct SetupArgs {
   const float4* trig;     // rotations: the map's pair tables, rows [H] then columns [W]
   float4* rtab;           // rotations: per-rotation tables
   long long rt_stride;
+  float* pixE;            // translations: synthesise the extended map [C][HE][WE] instead of pix
+  int HE, WE;
 };
 
 __device__ __forceinline__ float synth_pixel(const float* cf, int i, int j, int W, int n, int q) {
@@ -1326,6 +1436,31 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
       float4* o = reinterpret_cast<float4*>(a.pix) + 2 * e;
       o[0] = make_float4(v[0], v[1], v[2], v[3]);
       o[1] = make_float4(v[4], v[5], 0.0f, 0.0f);
+      return;
+    }
+    if (a.pixE != nullptr) {
+      // the extended map: each synthesised pixel (i, j) goes to every place it
+      // appears there.  Extended rows: one period (SPHERE: the map's rows,
+      // then the rows mirrored across the pole half a turn round; TORUS: the
+      // map's rows) and its first 65 rows again; extended columns: the map's
+      // columns and its first 68 again.
+      if (e >= N * a.C) return;
+      const int c = (int)(e / N);
+      const long long rem = e - (long long)c * N;
+      const int i = (int)(rem / a.W), j = (int)(rem - (long long)i * a.W);
+      const float v = synth_pixel(a.cin + (long long)c * a.cin_stride, i, j, a.W, a.n, a.q);
+      float* E = a.pixE + (long long)c * a.HE * a.WE;
+      const bool sph = a.boundary == HAAR_BOUNDARY_SPHERE;
+      const int per = sph ? 2 * a.H : a.H;
+      // rows i + k per, columns j + m W (and, SPHERE, the mirrored rows
+      // 2H - 1 - i + k per at column (j - W/2) mod W + m W)
+#pragma unroll 1
+      for (int mir = 0; mir < (sph ? 2 : 1); ++mir) {
+        const int ei0 = mir ? 2 * a.H - 1 - i : i;
+        const int ej0 = mir ? (j - (a.W >> 1)) & (a.W - 1) : j;
+        for (int ei = ei0; ei < a.HE; ei += per)
+          for (int ej = ej0; ej < a.WE; ej += a.W) E[(long long)ei * a.WE + ej] = v;
+      }
       return;
     }
     if (e >= N * a.C) return;
@@ -1508,14 +1643,32 @@ static bool tr8_eligible(const ShiftArgs& a, int S) {
 }
 
 static haar_status_t launch_tr8(const ShiftArgs& a, int S, cudaStream_t st) {
-  const size_t fl = 84 * (size_t)a.g.C + 4 + (((size_t)a.g.n_tiles + 3) & ~(size_t)3) + (size_t)a.g.n_tiles / 4 + 16;
+  const bool tma = a.pixE != nullptr;
+  const size_t fl = (tma ? kTr8Windows * (size_t)kTr8WinFloats + 32 : 0) + 84 * (size_t)a.g.C + 4 +
+                    (((size_t)a.g.n_tiles + 3) & ~(size_t)3) + (size_t)a.g.n_tiles / 4 + 16;
   const size_t sm = ((fl + 3) & ~(size_t)3) * sizeof(float);
-  auto fn = k_shift_tr8;
+  CUtensorMap mapP;
+  memset(&mapP, 0, sizeof(mapP));
+  if (tma && !encode_3d_f32(&mapP, a.pixE, (uint64_t)a.WE, (uint64_t)a.HE, (uint64_t)a.g.C, kTr8WinCols, kTr8WinRows))
+    return set_error(HAAR_ERR_CUDA, "haar_shift: cuTensorMapEncodeTiled (extended map) failed");
+  auto fn = tma ? k_shift_tr8<true, kTr8Windows> : k_shift_tr8<false, kTr8Windows>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_tr8)");
   }
-  return cuda_check(launch_pdl(fn, dim3(a.g.n_tiles, S), dim3(kTr8Threads), sm, st, a), "k_shift_tr8 launch");
+  return cuda_check(launch_pdl(fn, dim3(a.g.n_tiles, S), dim3(kTr8Threads), sm, st, a, mapP), "k_shift_tr8 launch");
+}
+
+bool tr8_tma_plan(const haar_shift_desc_t& d, const Geometry& g, int K, int max_shifts) {
+  return d.kind == HAAR_SHIFT_TRANSLATE && d.out_type == HAAR_OUT_F32 && d.out_layout == HAAR_LAYOUT_SCK &&
+         g.T == 64 && K >= g.N && g.H >= 64 && (long long)g.n_tiles * max_shifts >= 2432;
+}
+
+// this launch runs the TMA-fed batch kernel (the set-up then synthesises the
+// extended map instead of the plain one)
+static bool tr8_tma_use(const haar_shift_plan_s* p, int S, const void* out) {
+  return p->pixE != nullptr && p->desc.kind == HAAR_SHIFT_TRANSLATE && (long long)p->geo.n_tiles * S >= 2432 &&
+         (reinterpret_cast<uintptr_t>(out) & 15) == 0;
 }
 
 template <int KIND, int OUT>
@@ -1559,7 +1712,7 @@ haar_status_t launch_trig(haar_shift_plan_s* p, cudaStream_t st) {
   return cuda_check(cudaGetLastError(), "k_trig launch");
 }
 
-haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const double* params,
+haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const double* params, const void* out,
                            int S, cudaStream_t st) {
   SetupArgs a;
   const Geometry& g = p->geo;
@@ -1568,6 +1721,10 @@ haar_status_t launch_setup(haar_shift_plan_s* p, const float* coeffs_in, const d
   a.boundary = g.boundary;
   a.S = S;
   const bool rot = a.kind == HAAR_SHIFT_ROTATE || a.kind == HAAR_SHIFT_ROTATE_EULER;
+  const bool ext = tr8_tma_use(p, S, out);
+  a.pixE = ext ? p->pixE : nullptr;
+  a.HE = p->pixE_H;
+  a.WE = p->pixE_W;
   const long long total = rot ? g.N * ((g.C + 2) / 3) : g.N * g.C;
   a.nbp = (int)((total + kThreads - 1) / kThreads);
   a.cin = coeffs_in;
@@ -1676,6 +1833,12 @@ haar_status_t launch_shift(haar_shift_plan_s* p, const float* coeffs_in, int S, 
   a.scale = 1.0f;
   a.u_scale = (float)(g.H / 3.14159265358979323846);
   a.v_scale = (float)(g.W / (2.0 * 3.14159265358979323846));
+  a.status = p->status;
+  if (tr8_tma_use(p, S, out)) {
+    a.pixE = p->pixE;
+    a.HE = p->pixE_H;
+    a.WE = p->pixE_W;
+  }
   if (p->desc.kind == HAAR_SHIFT_TRANSLATE) return launch_out<KIND_TRANSLATE>(a, p->desc.out_type, S, st);
   return launch_out<KIND_ROTATE>(a, p->desc.out_type, S, st);
 }

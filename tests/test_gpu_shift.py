@@ -116,7 +116,7 @@ def test_dyadic_shifts_bit_exact(hs, H, W, boundary, layout):
 
 
 @pytest.mark.parametrize("boundary", [SPH, TOR])
-@pytest.mark.parametrize("H,W", [(128, 256), (256, 512)])
+@pytest.mark.parametrize("H,W", [(64, 128), (128, 256), (256, 512)])
 def test_dyadic_shifts_bit_exact_batch(hs, H, W, boundary):
     # enough shifts for the 8 x 8-block batch kernel (>= 2432 tile-shifts):
     # integer shifts that are multiples of 2^l give signed permutations of
