@@ -805,8 +805,11 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift
 // F32 translations into a k-contiguous layout (batches of many shifts):
 // CTA = one 64 x 64 output tile of one shift, all channels, thread per 8 x 8
 // block of output pixels (64 threads).  Per channel a thread streams the 9
-// source rows of its block's window (3 aligned float4 loads per row, the
-// rows' offsets computed once per thread), lerps each row horizontally and
+// source rows of its block's window (3 aligned float4 loads per row) from
+// the tile's window staged in shared memory by one TMA box of the plan's
+// extended map, or, without that map, from the pixel map with the rows'
+// offsets (pole mirroring, column wrap) computed once per thread; it lerps
+// each row horizontally and
 // each pair of rows vertically (weights pre-scaled by 1/2, exact), and
 // finishes levels 1-3 of its block in registers: level-1 details leave as
 // one float4 per row and band, level 2 as float2, level 3 as scalars.  The
