@@ -993,16 +993,47 @@ __device__ __forceinline__ void tr8_channels(const ShiftArgs& a, const ShiftPara
 }
 
 // The TMA-fed form: the tile's source window of every channel (65 rows x 68
-// columns of the extended map, one box) arrives in shared memory by a TMA
-// load, two channels' windows in flight; the threads read their block rows
-// there (offsets off[r] within the window).
-constexpr int kTr8WinRows = 65, kTr8WinCols = 68;
+// columns of the extended map) arrives in shared memory by TMA as eight bands
+// of 8 rows and the last row, each box 72 columns wide; the odd bands start 4
+// columns earlier in the map, so their rows sit 4 floats (4 banks) further on
+// in shared memory.  With one 65 x 68 box every block row of a warp (rows 8
+// apart) started on the same banks; the bands spread a warp's 16-byte reads
+// over twice as many bank groups: 7.77 M -> 5.83 M shared-load wavefronts for
+// 512 shifts of RGB 128x256, and 0.418 -> 0.405 ms for 4096.  (Those reads
+// are served 8 lanes at a time, and within 8 lanes, one block row, columns
+// 32 floats apart still share banks; a thread-to-block assignment that gave
+// each 8 lanes two block rows measured slower: 0.408 ms at 96 registers,
+// 0.454 ms with spills at 72.)
+constexpr int kTr8WinRows = 65, kTr8WinCols = 68;       // the window a tile reads
+constexpr int kTr8BoxCols = 72, kTr8BandRows = 8, kTr8Bands = 8;
+constexpr int kTr8BandFloats = kTr8BandRows * kTr8BoxCols;          // 576 floats = 18 x 128 bytes
+constexpr int kTr8WinFloats = kTr8Bands * kTr8BandFloats + 96;      // + the last row, a 128-byte multiple
+constexpr unsigned kTr8WinBytes = (kTr8Bands * kTr8BandRows + 1) * kTr8BoxCols * 4;
+static_assert(kTr8Bands * kTr8BandRows + 1 == kTr8WinRows && kTr8BoxCols >= kTr8WinCols + 4, "window boxes");
 // one window per CTA (the next channel's copy issued once the current one is
-// read): 17.8 KB of shared memory, 12 CTAs per SM; two windows in flight
-// (35.6 KB, 6 CTAs per SM) measured slower (0.498 against 0.418 ms for 4096
-// shifts of RGB 128x256), as did the direct loads (0.439 ms)
+// read): 18.8 KB of shared memory; two windows in flight (6 CTAs per SM)
+// measured slower (0.498 against 0.418 ms for 4096 shifts of RGB 128x256
+// with the single-box window), as did the direct loads (0.439 ms)
 constexpr int kTr8Windows = 1;
-constexpr int kTr8WinFloats = 4448;              // 65 x 68 rounded up to a 128-byte multiple
+
+// offset in the staged window of window row R (0..64), block column bx
+__device__ __forceinline__ int tr8_win_off(int R, int bx) {
+  const int b = R >> 3;
+  return b * kTr8BandFloats + (R & 7) * kTr8BoxCols + 4 * (b & 1) + 8 * bx;
+}
+
+// issue the window of channel c (map columns from xw, rows from yw) into w:
+// the bands by mapB (72 x 8 boxes; odd bands from column xw - 4, which for
+// xw = 0 reads the zero fill left of the map, columns no thread uses), the
+// last row by mapR (a 72 x 1 box); all of it completes on barrier `bar`
+__device__ __forceinline__ void tr8_issue(float* w, const CUtensorMap* mapB, const CUtensorMap* mapR, int xw,
+                                          int yw, int c, uint32_t bar) {
+  tc::mbar_arrive_tx(bar, kTr8WinBytes);
+#pragma unroll
+  for (int b = 0; b < kTr8Bands; ++b)
+    tc::tma_load_3d(tc::smem_u32(w + b * kTr8BandFloats), mapB, xw - 4 * (b & 1), yw + kTr8BandRows * b, c, bar);
+  tc::tma_load_3d(tc::smem_u32(w + kTr8Bands * kTr8BandFloats), mapR, xw, yw + kTr8Bands * kTr8BandRows, c, bar);
+}
 constexpr unsigned long long kTr8WaitNs = 2000000000ull;
 
 // bounded wait on a window's barrier; false (status set) on expiry
@@ -1020,8 +1051,8 @@ __device__ __forceinline__ bool tr8_wait(uint32_t bar, uint32_t parity, int* sta
 template <int O, int NB>
 __device__ __forceinline__ void tr8_channels_tma(const ShiftArgs& a, const ShiftParam& pr, int s, const int (&off)[9],
                                                  int i0, int j0, float* sA3, float* win, uint64_t* wbar,
-                                                 int* wissued, int* wdone, const CUtensorMap* mapP, int xw, int yw,
-                                                 int* s_fail) {
+                                                 int* wissued, int* wdone, const CUtensorMap* mapP,
+                                                 const CUtensorMap* mapR, int xw, int yw, int* s_fail) {
   const Geometry& g = a.g;
 #pragma unroll 1
   for (int c = 0; c < g.C; ++c) {
@@ -1036,8 +1067,7 @@ __device__ __forceinline__ void tr8_channels_tma(const ShiftArgs& a, const Shift
     __syncthreads();                                // every thread is done with this window
     if (threadIdx.x == 0 && ok && c + NB < g.C) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc::mbar_arrive_tx(tc::smem_u32(&wbar[b]), kTr8WinRows * kTr8WinCols * 4);
-      tc::tma_load_3d(tc::smem_u32(w), mapP, xw, yw, c + NB, tc::smem_u32(&wbar[b]));
+      tr8_issue(w, mapP, mapR, xw, yw, c + NB, tc::smem_u32(&wbar[b]));
       ++wissued[b];
     }
   }
@@ -1045,7 +1075,8 @@ __device__ __forceinline__ void tr8_channels_tma(const ShiftArgs& a, const Shift
 
 // 72 registers (14 CTAs per SM); 64 or 80 measured slower
 template <bool TMA, int NB>
-__global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, const __grid_constant__ CUtensorMap mapP) {
+__global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, const __grid_constant__ CUtensorMap mapP,
+                                                                      const __grid_constant__ CUtensorMap mapR) {
   extern __shared__ __align__(16) float smem[];
   __shared__ ShiftParam s_prm;
   __shared__ int s_last;
@@ -1097,7 +1128,8 @@ __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, cons
     if (yw < 0) yw += per;
     const int xw = (tc * g.T - pr.kx - 1 - o) & Wm;
 #pragma unroll
-    for (int r = 0; r < 9; ++r) off[r] = (8 * by + r) * kTr8WinCols + 8 * bx;
+    for (int r = 0; r < 8; ++r) off[r] = tr8_win_off(8 * by, bx) + r * kTr8BoxCols;   // band by
+    off[8] = tr8_win_off(8 * by + 8, bx);                                               // first row of band by + 1
     if (threadIdx.x == 0) {
       s_fail = 0;
       wdone[0] = wdone[1] = 0;
@@ -1106,17 +1138,16 @@ __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, cons
       tc::mbar_init(tc::smem_u32(&wbar[1]), 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       for (int c = 0; c < NB && c < g.C; ++c) {
-        tc::mbar_arrive_tx(tc::smem_u32(&wbar[c]), kTr8WinRows * kTr8WinCols * 4);
-        tc::tma_load_3d(tc::smem_u32(win + c * kTr8WinFloats), &mapP, xw, yw, c, tc::smem_u32(&wbar[c]));
+        tr8_issue(win + c * kTr8WinFloats, &mapP, &mapR, xw, yw, c, tc::smem_u32(&wbar[c]));
         wissued[c] = 1;
       }
     }
     __syncthreads();
     switch (o) {
-      case 0: tr8_channels_tma<0, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
-      case 1: tr8_channels_tma<1, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
-      case 2: tr8_channels_tma<2, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
-      default: tr8_channels_tma<3, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, xw, yw, &s_fail); break;
+      case 0: tr8_channels_tma<0, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, &mapR, xw, yw, &s_fail); break;
+      case 1: tr8_channels_tma<1, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, &mapR, xw, yw, &s_fail); break;
+      case 2: tr8_channels_tma<2, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, &mapR, xw, yw, &s_fail); break;
+      default: tr8_channels_tma<3, NB>(a, pr, s, off, i0, j0, sA3, win, wbar, wissued, wdone, &mapP, &mapR, xw, yw, &s_fail); break;
     }
     if (s_fail) {
       // a window never arrived: let any copy still in flight land (bounded)
@@ -1650,16 +1681,20 @@ static haar_status_t launch_tr8(const ShiftArgs& a, int S, cudaStream_t st) {
   const size_t fl = (tma ? kTr8Windows * (size_t)kTr8WinFloats + 32 : 0) + 84 * (size_t)a.g.C + 4 +
                     (((size_t)a.g.n_tiles + 3) & ~(size_t)3) + (size_t)a.g.n_tiles / 4 + 16;
   const size_t sm = ((fl + 3) & ~(size_t)3) * sizeof(float);
-  CUtensorMap mapP;
+  CUtensorMap mapP, mapR;            // the window's 72 x 8 bands and its 72 x 1 last row
   memset(&mapP, 0, sizeof(mapP));
-  if (tma && !encode_3d_f32(&mapP, a.pixE, (uint64_t)a.WE, (uint64_t)a.HE, (uint64_t)a.g.C, kTr8WinCols, kTr8WinRows))
+  memset(&mapR, 0, sizeof(mapR));
+  if (tma && (!encode_3d_f32(&mapP, a.pixE, (uint64_t)a.WE, (uint64_t)a.HE, (uint64_t)a.g.C, kTr8BoxCols,
+                             kTr8BandRows) ||
+              !encode_3d_f32(&mapR, a.pixE, (uint64_t)a.WE, (uint64_t)a.HE, (uint64_t)a.g.C, kTr8BoxCols, 1)))
     return set_error(HAAR_ERR_CUDA, "haar_shift: cuTensorMapEncodeTiled (extended map) failed");
   auto fn = tma ? k_shift_tr8<true, kTr8Windows> : k_shift_tr8<false, kTr8Windows>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(k_shift_tr8)");
   }
-  return cuda_check(launch_pdl(fn, dim3(a.g.n_tiles, S), dim3(kTr8Threads), sm, st, a, mapP), "k_shift_tr8 launch");
+  return cuda_check(launch_pdl(fn, dim3(a.g.n_tiles, S), dim3(kTr8Threads), sm, st, a, mapP, mapR),
+                    "k_shift_tr8 launch");
 }
 
 bool tr8_tma_plan(const haar_shift_desc_t& d, const Geometry& g, int K, int max_shifts) {
