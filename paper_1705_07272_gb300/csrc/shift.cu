@@ -44,6 +44,7 @@ struct ShiftArgs {
   const float4* rtab;     // rotations: per-rotation tables, rt_stride float4 apart
   long long rt_stride;
   int tab_off;            // rotations, tables in shared memory: their offset in floats
+  int tail_off = 0;       // translation batch kernel: the tail's offset in floats (tr8_tail_floats)
   float scale;
   float u_scale, v_scale; // H/pi, W/(2 pi)
   const float* pixE = nullptr;   // translation batches: the extended map (see haar_shift_plan_s::pixE)
@@ -978,8 +979,9 @@ __device__ __forceinline__ void tr8_level(const ShiftArgs& a, const ShiftParam& 
   }
 }
 
-// Shared memory (floats): level-3 means [C][64], level-4 [C][16], level-5
-// [C][4], then (last CTA of a shift) the tile-mean image and its scratch.
+// Shared memory (floats): level-3 means [C][64], then the tail
+// (tr8_tail_floats): level-4 [C][16], level-5 [C][4], level-6 [C] and (last
+// CTA of a shift) the tile-mean image and its scratch.
 template <int O>
 __device__ __forceinline__ void tr8_channels(const ShiftArgs& a, const ShiftParam& pr, int s, const int (&off)[9],
                                              bool wrap, int i0, int j0, float* sA3) {
@@ -1015,6 +1017,18 @@ static_assert(kTr8Bands * kTr8BandRows + 1 == kTr8WinRows && kTr8BoxCols >= kTr8
 // measured slower (0.498 against 0.418 ms for 4096 shifts of RGB 128x256
 // with the single-box window), as did the direct loads (0.439 ms)
 constexpr int kTr8Windows = 1;
+
+// Shared floats of the kernel's tail, which runs after the last window is
+// consumed: the level means [C][16], [C][4] and [C] (rounded up to 4) and,
+// in the last CTA of a shift, the tile-mean image and its next level.  The
+// TMA-fed form puts the tail in the window's shared memory when it fits.
+static long long tr8_tail_floats(int C, long long n_tiles) {
+  return 20LL * C + ((C + 3) & ~3) + ((n_tiles + 3) & ~3LL) + ((n_tiles / 4 + 4) & ~3LL);
+}
+
+static bool tr8_tail_in_window(bool tma, int C, long long n_tiles) {
+  return tma && tr8_tail_floats(C, n_tiles) <= (long long)kTr8Windows * kTr8WinFloats;
+}
 
 // offset in the staged window of window row R (0..64), block column bx
 __device__ __forceinline__ int tr8_win_off(int R, int bx) {
@@ -1115,9 +1129,7 @@ __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, cons
   // TMA: two windows at a 128-byte aligned start (the launch adds 128 bytes)
   float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
   float* sA3 = TMA ? win + NB * kTr8WinFloats : smem;
-  float* sA4 = sA3 + 64 * g.C;
-  float* sA5 = sA4 + 16 * g.C;
-  float* sA6 = sA5 + 4 * g.C;
+  float* sA4 = TMA ? win : sA3 + 64 * g.C;   // the tail (see below)
   if (TMA) {
     __shared__ uint64_t wbar[2];
     __shared__ int s_fail, wissued[2], wdone[2];
@@ -1168,6 +1180,12 @@ __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, cons
     }
   }
   pdl_trigger();
+  // the tail (levels 4-6, the coarse pass): in the window's shared memory
+  // when it fits (every window has been read: the last barrier of the
+  // channel loop), else after the level-3 means
+  if (TMA) sA4 += a.tail_off;
+  float* sA5 = sA4 + 16 * g.C;
+  float* sA6 = sA5 + 4 * g.C;
   __syncthreads();
   tr8_level(a, pr, s, 4, 4, sA3, sA4, tr, tc);
   __syncthreads();
@@ -1676,10 +1694,15 @@ static bool tr8_eligible(const ShiftArgs& a, int S) {
          (reinterpret_cast<uintptr_t>(a.out) & 15) == 0 && (long long)a.g.n_tiles * S >= 2432;
 }
 
-static haar_status_t launch_tr8(const ShiftArgs& a, int S, cudaStream_t st) {
+static haar_status_t launch_tr8(const ShiftArgs& a0, int S, cudaStream_t st) {
+  ShiftArgs a = a0;
   const bool tma = a.pixE != nullptr;
-  const size_t fl = (tma ? kTr8Windows * (size_t)kTr8WinFloats + 32 : 0) + 84 * (size_t)a.g.C + 4 +
-                    (((size_t)a.g.n_tiles + 3) & ~(size_t)3) + (size_t)a.g.n_tiles / 4 + 16;
+  const bool tail_win = tr8_tail_in_window(tma, a.g.C, a.g.n_tiles);
+  a.tail_off = tail_win ? 0 : (tma ? kTr8Windows * kTr8WinFloats : 0) + 64 * a.g.C;
+  // [window (TMA-fed form; + 32 for its 128-byte alignment) | level-3 means
+  // [C][64] | the tail, unless it sits in the window]
+  const size_t fl = (tma ? kTr8Windows * (size_t)kTr8WinFloats + 32 : 0) + 64 * (size_t)a.g.C +
+                    (tail_win ? 0 : (size_t)tr8_tail_floats(a.g.C, a.g.n_tiles));
   const size_t sm = ((fl + 3) & ~(size_t)3) * sizeof(float);
   CUtensorMap mapP, mapR;            // the window's 72 x 8 bands and its 72 x 1 last row
   memset(&mapP, 0, sizeof(mapP));

@@ -299,10 +299,11 @@ def test_full_size_translation_batch(hs):
     assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
 
 
-@pytest.mark.parametrize("C,boundary", [(4, SPH), (1, TOR)])
+@pytest.mark.parametrize("C,boundary", [(4, SPH), (1, TOR), (24, SPH)])
 def test_translation_many_shifts_channel_groups(hs, C, boundary):
-    # enough shifts for the three-channels-per-thread launch, with a partial
-    # channel group (C = 4) and a single channel
+    # enough shifts for the batch kernel, with a partial channel group (C =
+    # 4), a single channel, and 24 channels (the batch kernel's per-channel
+    # level means then no longer fit the slack of a fixed shared-memory tail)
     H, W = 128, 256
     c = _lighting(C, H, W, 31 + C)
     rng = np.random.default_rng(C)
