@@ -295,6 +295,21 @@ __device__ void coarse_levels_t(const ShiftArgs& a, const ShiftParam* p, int s, 
   if (WARP) __syncwarp(); else __syncthreads();
 }
 
+// img[k] = src[k] for k < n by threads tid, tid + nthr, ...: eight L2 loads
+// in flight per thread (a loop of load -> shared store pairs waits one L2
+// round trip per element: 8 of them for the 128 tile means of a 16 x 16-tile
+// plane at 16 threads per plane)
+__device__ __forceinline__ void gather_means(float* img, const float* src, int n, int tid, int nthr) {
+  for (int k0 = tid; k0 < n; k0 += 8 * nthr) {
+    float r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = (k0 + u * nthr < n) ? __ldcg(src + k0 + u * nthr) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u * nthr < n) img[k0 + u * nthr] = r[u];
+  }
+}
+
 template <int OUT>
 __device__ __forceinline__ void coarse_levels(const ShiftArgs& a, const ShiftParam* p, int s, int c, float* img,
                                               float* img2) {
@@ -413,8 +428,7 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   float* img = pbuf;
   float* img2 = pbuf + ((g.n_tiles + 3) & ~3);   // float4-aligned
   for (int c = 0; c < g.C; ++c) {
-    for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
-      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
+    gather_means(img, a.means + ((long long)s * g.C + c) * g.n_tiles, (int)g.n_tiles, threadIdx.x, blockDim.x);
     coarse_levels<OUT>(a, p, s, c, img, img2);
   }
   if (threadIdx.x == 0) a.counters[s] = 0u;
@@ -795,8 +809,7 @@ __global__ void __launch_bounds__(kThreads, KIND == KIND_ROTATE ? 3 : 4) k_shift
   float* img = smem + ((CG * groups + 3) & ~3);
   float* img2 = img + ((g.n_tiles + 3) & ~3);   // float4-aligned
   for (int c = 0; c < g.C; ++c) {
-    for (int t = lane; t < g.n_tiles; t += 32)
-      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
+    gather_means(img, a.means + ((long long)s * g.C + c) * g.n_tiles, (int)g.n_tiles, lane, 32);
     coarse_levels_warp<OUT>(a, p, s, c, img, img2, lane);
   }
   if (lane == 0) a.counters[s] = 0u;
@@ -1211,8 +1224,7 @@ __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, cons
   float* img = sA6 + ((g.C + 3) & ~3);
   float* img2 = img + ((g.n_tiles + 3) & ~3);
   for (int c = 0; c < g.C; ++c) {
-    for (int t = threadIdx.x; t < g.n_tiles; t += blockDim.x)
-      img[t] = __ldcg(a.means + ((long long)s * g.C + c) * g.n_tiles + t);
+    gather_means(img, a.means + ((long long)s * g.C + c) * g.n_tiles, (int)g.n_tiles, threadIdx.x, blockDim.x);
     coarse_levels<HAAR_OUT_F32>(a, &s_prm, s, c, img, img2);
   }
   if (threadIdx.x == 0) a.counters[s] = 0u;
@@ -1379,8 +1391,7 @@ __global__ void __launch_bounds__(16 * NP) k_shift_ksc(ShiftArgs a, int P) {
   const int per = ksc_plane_floats(g.n_tiles);
   float* img = smem + pl * per;
   float* img2 = img + nt4;
-  if (on)
-    for (int k = blk; k < g.n_tiles; k += 16) img[k] = __ldcg(a.means + (long long)plane * g.n_tiles + k);
+  if (on) gather_means(img, a.means + (long long)plane * g.n_tiles, (int)g.n_tiles, blk, 16);
   // threads of absent planes (partial group) take part in the barriers only
   coarse_levels_t<HAAR_OUT_F32, false>(a, pp, s, c, img, img2, on ? blk : (1 << 30), 16);
   if (t == 0) a.counters[blockIdx.y] = 0u;
