@@ -407,7 +407,12 @@ __global__ void __launch_bounds__(256, 3) k_shade_gcsr48(const float* __restrict
                                                            const int32_t* __restrict__ gptr, int V,
                                                            const float* __restrict__ L, int NL,
                                                            float* __restrict__ R) {
-  pdl_wait();                                     // inputs come from the previous kernel
+  // Only the lighting L comes from the previous kernel (the phase shift,
+  // launched as this kernel's programmatic primary).  The transport is read
+  // before waiting for it: the library's kernels that let dependents start
+  // early are the shift kernels, which do not write transport, and every
+  // frame's set-up is an ordinary launch (a full stream barrier).  So the
+  // first CTAs fetch their entry lists while the shift finishes.
   typedef unsigned long long u64;
   __shared__ u64 red[4][8][kGroup][3];
   __shared__ float4 sv[8][32];
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(256, 3) k_shade_gcsr48(const float* __restrict
     nv = ld_stream_f4(V4 + jb + lane);
     if (nk >= NL) { nk = 0; nv = make_float4(0.f, 0.f, 0.f, 0.f); }
   }
+  pdl_wait();                                     // the lighting is complete
   for (int j0 = jb; j0 < je; j0 += 32) {
     const int myk = nk;
     __syncwarp();
