@@ -271,8 +271,8 @@ def test_bincsr_small(hs):
             Tv[v, idx[v, b[v]]] = vals16[v, b[v]]
         ref[:, s] = np.einsum("vk,ck->vc", Tv, Ls[s])
     ok = (margin > 1e-5).T
-    assert rel_l2(got[ok], ref[ok]) <= 2e-3
-    assert rel_l2(got[ok], ref[ok]) <= 1e-4
+    assert rel_l2(got[ok], ref[ok]) <= 2e-3            # the benchmark spec's FP16 bar
+    assert rel_l2(got[ok], ref[ok]) <= 1e-5            # FP16 values are exact in FP32; FP32 sums
     # the same frame with the lighting in SKC4 (16-byte gathers): identical sums
     plan4 = hs.Plan(H, W, 3, kind=hs.HAAR_SHIFT_ROTATE_EULER, max_shifts=S, out_layout=hs.HAAR_LAYOUT_SKC4)
     R4 = hs.shade_batch(plan4, _t(L, torch.float32), _t(sc["params"], torch.float64), tr)
