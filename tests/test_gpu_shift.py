@@ -317,6 +317,20 @@ def test_translation_many_shifts_channel_groups(hs, C, boundary):
     assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
 
 
+def test_maximum_map_size_translation(hs):
+    # the largest map a plan accepts: 4096 x 8192 (12 levels, 8192 tiles of
+    # 64 x 64), one channel, every coefficient of two fractional shifts against
+    # the oracle.  Two shifts already take the TMA-fed batch kernel, whose
+    # level means and coarse images (8192 tile means) then sit after the
+    # window in shared memory, not in it.
+    H, W = 4096, 8192
+    c = _lighting(1, H, W, 4096)
+    prm = np.array([[1234.37, -517.81], [-3000.5, 2222.25]])
+    got, _ = _run(hs, c, H, W, 0, prm)
+    ref = osh.haar_shift(c, H, W, osh.TRANSLATE, prm)
+    assert rel_l2(got, ref, axis=(1, 2)).max() <= 1e-5
+
+
 def test_full_size_rotation_batch(hs):
     # the bench's rotation row: 512 rotations of the RGB 256x512 map in one launch
     sc = synth.scene(2, V=1)
