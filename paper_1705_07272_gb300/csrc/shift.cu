@@ -1100,7 +1100,8 @@ __device__ __forceinline__ void tr8_channels_tma(const ShiftArgs& a, const Shift
   }
 }
 
-// 72 registers (14 CTAs per SM); 64 or 80 measured slower
+// 72 registers (room for 14 CTAs per SM; shared memory allows 11: the window,
+// the level-3 means and the tail in the window); 64 or 80 measured slower
 template <bool TMA, int NB>
 __global__ void __launch_bounds__(kTr8Threads, 14) k_shift_tr8(ShiftArgs a, const __grid_constant__ CUtensorMap mapP,
                                                                       const __grid_constant__ CUtensorMap mapR) {
